@@ -1,0 +1,163 @@
+/*
+ * sttsm.h — C ABI of the GB300 (sm_103a) library for the symmetric tensor
+ * times same matrix operation on Blocked Compact Symmetric Storage.
+ *
+ * Paper: M. D. Schatz, T. M. Low, R. A. van de Geijn, T. G. Kolda,
+ * "Exploiting Symmetry in Tensors for High Performance: Multiplication with
+ * Symmetric Tensors", arXiv 1301.7744.
+ *
+ * Operation (eq. (cob), Sec. 2.5):  C := [A; X, ..., X] = A x_0 X x_1 ... x_{m-1} X,
+ *   gamma_{j_0..j_{m-1}} = sum_{i in [0,n)^m} alpha_{i_0..i_{m-1}} prod_k chi_{j_k, i_k},
+ * with A an order-m symmetric tensor of dimension n, X a p x n matrix and C
+ * an order-m symmetric tensor of dimension p.
+ *
+ * Conventions used by every entry point:
+ *   - Indices are 0-based (Sec. 2.1).
+ *   - Dense tensors are in dimensional order (App. A): entry (i_0..i_{m-1})
+ *     at offset sum_k i_k n^k, mode 0 fastest.
+ *   - X is p x n, column-major: chi_{j,i} at X[j + i*p] (the libflame
+ *     convention the paper follows, Sec. 3.3).
+ *   - BCSS (Sec. 3.3, 4.3, 5.3; Tbl. 1): a tensor of dimension n is cut
+ *     into blocks of b^m entries, nbar = ceil(n/b) blocks per mode (App. B).
+ *     Only blocks with sorted block indices ibar_0 <= ... <= ibar_{m-1}
+ *     are stored: C(nbar+m-1, m) blocks.  Stored block with indices
+ *     (ibar_0..ibar_{m-1}) has rank sum_k C(ibar_k + k, k + 1) (colex order:
+ *     the last block index varies slowest, the order of the paper's loops;
+ *     for m = 2, b = 1 it is the element order pictured in Sec. 3.3).  A
+ *     block is a dense b^m array in dimensional order.  Block entries that
+ *     fall at an index >= n are padding and are zero.  Symmetry inside
+ *     diagonal blocks is not exploited (Sec. 3.3): diagonal blocks are
+ *     stored in full.
+ *   - Device pointers unless stated otherwise.  The caller owns every
+ *     buffer; the library never frees caller memory.  The library owns
+ *     only small per-shape plans (tile lists) it caches in device memory.
+ *   - Every call returns an sttsm_status (or a count); nothing throws
+ *     across the ABI.  Arguments are validated before any launch.  Work is
+ *     enqueued on `stream` (a cudaStream_t; 0 = legacy default stream).
+ *   - A and C must hold symmetric data; the library does not check it.
+ */
+#ifndef STTSM_H
+#define STTSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    STTSM_OK = 0,
+    STTSM_ERR_ARG = -1,          /* invalid argument (size, pointer, alignment) */
+    STTSM_ERR_UNSUPPORTED = -2,  /* valid but not implemented (e.g. m > 8, TF32X3) */
+    STTSM_ERR_NOMEM = -3,        /* workspace too small / plan allocation failed */
+    STTSM_ERR_TIMEOUT = -4,      /* a device-side bounded wait ran out (status word set) */
+    STTSM_ERR_CUDA = -5,         /* a CUDA runtime call failed */
+    STTSM_ERR_BUSY = -6          /* serving queue full */
+} sttsm_status;
+
+/* Arithmetic of the mode products.
+ *   STTSM_FP64:  A, X, C in FP64; FP64 FMAs on the CUDA cores.
+ *   STTSM_BF16X6: A, X, C in FP32; every FP32 operand is split into three
+ *                 BF16 pieces (hi, mid, lo) and the six piece products whose
+ *                 piece orders sum to <= 2 run on the tcgen05 tensor cores
+ *                 with FP32 accumulation in tensor memory.
+ *   STTSM_BF16X3: as BF16X6 with two pieces and three products (about 2^-16
+ *                 relative error per product: cheaper, less accurate).
+ *   STTSM_TF32X3: reserved; returns STTSM_ERR_UNSUPPORTED. */
+typedef enum { STTSM_FP64 = 0, STTSM_BF16X6 = 1, STTSM_TF32X3 = 2, STTSM_BF16X3 = 3 } sttsm_prec;
+
+/* Element types for bcss_pack / bcss_unpack. */
+typedef enum { STTSM_DTYPE_F64 = 0, STTSM_DTYPE_F32 = 1 } sttsm_dtype;
+
+/* ------------------------------------------------------------------ BCSS indexing (host) */
+
+/* Number of stored blocks, C(nbar + m - 1, m) (Tbl. 1).  -1 on bad arguments. */
+int64_t bcss_num_blocks(int m, int64_t n, int b);
+
+/* Number of stored entries, b^m C(nbar + m - 1, m) (Tbl. 1).  -1 on bad arguments. */
+int64_t bcss_num_elems(int m, int64_t n, int b);
+
+/* Colex rank of a non-decreasing block-index tuple (m entries), i.e. the
+ * position of that block in BCSS storage.  -1 if the tuple is not sorted or
+ * has a negative entry. */
+int64_t bcss_block_rank(int m, const int32_t* sorted_blk_idx);
+
+/* Inverse of bcss_block_rank: writes the sorted tuple of the block stored
+ * at `rank` into blk_idx_out[0..m-1].  STTSM_ERR_ARG if rank < 0. */
+int bcss_block_unrank(int m, int64_t rank, int32_t* blk_idx_out);
+
+/* Flops of the algorithm-by-blocks with partially symmetric temporaries,
+ * Tbl. 4 (MinCosts), BCSS computation row with b_A = b_C = b:
+ *   2 nbar b^{m+1} sum_{d=0}^{m-1} C(pbar+d, d+1) C(nbar+m-d-2, m-d-1).
+ * This is the useful-flop count that throughput figures are quoted in. */
+double sttsm_flops(int m, int64_t n, int64_t p, int b);
+
+/* ------------------------------------------------------------------ BCSS packing (device) */
+
+/* Dense (n^m, dimensional order) -> BCSS.  Reads, for every stored block,
+ * the dense entries at its block indices; writes zeros at padding entries.
+ * dense: n^m elements; bcss: bcss_num_elems(m,n,b) elements; dtype as
+ * sttsm_dtype.  The copy is bit-exact.  1 <= m <= 8, n >= 1, b >= 1. */
+int bcss_pack(const void* dense, void* bcss, int m, int64_t n, int b, int dtype, void* stream);
+
+/* BCSS -> dense.  Entry (i_0..i_{m-1}) is read from the block of the sorted
+ * block indices at the sorted in-block indices (the canonical entry), so
+ * the dense result is exactly symmetric even where the stored diagonal
+ * blocks carry rounding asymmetry (Sec. 5.4 mentions this asymmetry and a
+ * post-processing step; this is that step).  Bit-exact copy. */
+int bcss_unpack(const void* bcss, void* dense, int m, int64_t n, int b, int dtype, void* stream);
+
+/* ------------------------------------------------------------------ sttsm (device) */
+
+/* Bytes of device workspace sttsm_bcss needs: the two ping-pong buffers
+ * holding the unique blocks of the partially symmetric temporaries
+ * T^(m-1) ... T^(1) (Thm. 1; Tbl. 4 "All temporaries"), one level at a time,
+ * plus the split pieces of X for the tensor-core precisions. */
+int sttsm_workspace_size(int m, int64_t n, int64_t p, int b, int prec, size_t* bytes);
+
+/* C := [A; X, ..., X] on BCSS (Sec. 5.4 algorithm-by-blocks, Fig. 5, with
+ * Thm. 1's partial symmetry exploited in every temporary, Sec. 6.3).
+ *   A_bcss: bcss_num_elems(m, n, b) elements (FP64 for STTSM_FP64, else FP32).
+ *   X:      p x n column-major, same element type.
+ *   C_bcss: bcss_num_elems(m, p, b) elements, written in full (padding
+ *           entries become zero).
+ *   workspace: >= sttsm_workspace_size bytes, 256-byte aligned.
+ * 1 <= m <= 8; b^{m-1} < 2^31; all pointers 16-byte aligned.  Asynchronous
+ * on `stream`.  Returns STTSM_ERR_TIMEOUT if a previous launch on this
+ * device recorded a bounded-wait timeout (the status word is then cleared). */
+int sttsm_bcss(const void* A_bcss, const void* X, int m, int64_t n, int64_t p, int b,
+               void* C_bcss, int prec, void* workspace, size_t ws_bytes, void* stream);
+
+/* End-to-end variant on HOST buffers: copies A_bcss and X (host, ideally
+ * pinned) to the device buffers dA and dX, runs sttsm_bcss, copies C back
+ * to the host buffer C_bcss, all enqueued on `stream` (synchronise the
+ * stream before reading C_bcss). dA, dX, dC, workspace are device buffers
+ * of the sizes sttsm_bcss needs. */
+int sttsm_bcss_host(const void* A_bcss, const void* X, int m, int64_t n, int64_t p, int b,
+                    void* C_bcss, int prec, void* dA, void* dX, void* dC,
+                    void* workspace, size_t ws_bytes, void* stream);
+
+/* Device status word: 0 = fine; otherwise the code of the last device-side
+ * failure (1 = bounded wait timed out).  Reading clears it. */
+int sttsm_device_status(void);
+
+/* ------------------------------------------------------------------ diagnostics (host) */
+
+/* The plan sttsm_bcss runs at level d (0 <= d < m; level d reads T^(m-d) and
+ * writes T^(m-1-d), Fig. 5) for precision `prec` (which fixes the tile
+ * shape).  Host buffers; pass NULL buffers to query the sizes.
+ *   tiles:  ntiles x 8 int32 (inst, parent node, first child node, first row,
+ *           first column, columns, 0, 0), capacity tiles_cap tiles;
+ *   G:      P_out x nbar int32 gather table, (rank << 3) | q, capacity G_cap;
+ *   info:   9 int64: k, P_parent, P_out, rows per parent, parent nodes,
+ *           child nodes, rows per block R = b^(m-1), b^m, tile rows BM.
+ * Returns STTSM_ERR_NOMEM if a capacity is too small. */
+int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_t* tiles, int64_t tiles_cap,
+                     int32_t* G, int64_t G_cap, int64_t* ntiles_out, int64_t* nG_out, int64_t* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,238 @@
+"""Python binding of libsttsm (the C ABI in include/sttsm.h).
+
+Argument marshalling only: every step of sttsm runs in the library's CUDA
+kernels.  Device buffers are torch tensors (their data_ptr is passed);
+streams are torch CUDA streams (default: the current stream).  Names and
+argument order follow the C ABI.
+
+Paper: Schatz, Low, van de Geijn, Kolda, "Exploiting Symmetry in Tensors for
+High Performance: Multiplication with Symmetric Tensors", arXiv 1301.7744.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+_PKG = Path(__file__).resolve().parent
+_LIB_PATH = _PKG / "_lib" / "libsttsm.so"
+
+STTSM_OK = 0
+STTSM_ERR_ARG = -1
+STTSM_ERR_UNSUPPORTED = -2
+STTSM_ERR_NOMEM = -3
+STTSM_ERR_TIMEOUT = -4
+STTSM_ERR_CUDA = -5
+STTSM_ERR_BUSY = -6
+
+STTSM_FP64 = 0
+STTSM_BF16X6 = 1
+STTSM_TF32X3 = 2
+STTSM_BF16X3 = 3
+
+DTYPE_F64 = 0
+DTYPE_F32 = 1
+
+PREC_NAMES = {STTSM_FP64: "fp64", STTSM_BF16X6: "bf16x6", STTSM_TF32X3: "tf32x3", STTSM_BF16X3: "bf16x3"}
+_ERRORS = {STTSM_ERR_ARG: "invalid argument", STTSM_ERR_UNSUPPORTED: "unsupported",
+           STTSM_ERR_NOMEM: "workspace too small or allocation failed", STTSM_ERR_TIMEOUT: "device wait timed out",
+           STTSM_ERR_CUDA: "CUDA call failed", STTSM_ERR_BUSY: "queue full"}
+
+
+class SttsmError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__("%s returned %d (%s)" % (fn, code, _ERRORS.get(code, "?")))
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> Path:
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise RuntimeError("libsttsm.so is not built (%s); run __graft_entry__.build()" % _LIB_PATH)
+    L = ctypes.CDLL(str(_LIB_PATH))
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.bcss_num_blocks.argtypes = [i32, i64, i32]
+    L.bcss_num_blocks.restype = i64
+    L.bcss_num_elems.argtypes = [i32, i64, i32]
+    L.bcss_num_elems.restype = i64
+    L.bcss_block_rank.argtypes = [i32, P]
+    L.bcss_block_rank.restype = i64
+    L.bcss_block_unrank.argtypes = [i32, i64, P]
+    L.bcss_block_unrank.restype = i32
+    L.sttsm_flops.argtypes = [i32, i64, i64, i32]
+    L.sttsm_flops.restype = ctypes.c_double
+    L.bcss_pack.argtypes = [P, P, i32, i64, i32, i32, P]
+    L.bcss_pack.restype = i32
+    L.bcss_unpack.argtypes = [P, P, i32, i64, i32, i32, P]
+    L.bcss_unpack.restype = i32
+    L.sttsm_workspace_size.argtypes = [i32, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.sttsm_workspace_size.restype = i32
+    L.sttsm_bcss.argtypes = [P, P, i32, i64, i64, i32, P, i32, P, ctypes.c_size_t, P]
+    L.sttsm_bcss.restype = i32
+    L.sttsm_bcss_host.argtypes = [P, P, i32, i64, i64, i32, P, i32, P, P, P, P, ctypes.c_size_t, P]
+    L.sttsm_bcss_host.restype = i32
+    L.sttsm_device_status.argtypes = []
+    L.sttsm_device_status.restype = i32
+    L.sttsm_plan_level.argtypes = [i32, i64, i64, i32, i32, i32, P, i64, P, i64, P, P, P]
+    L.sttsm_plan_level.restype = i32
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C-ABI entry points this binding loads."""
+    return ["bcss_num_blocks", "bcss_num_elems", "bcss_block_rank", "bcss_block_unrank", "sttsm_flops",
+            "bcss_pack", "bcss_unpack", "sttsm_workspace_size", "sttsm_bcss", "sttsm_bcss_host",
+            "sttsm_device_status", "sttsm_plan_level"]
+
+
+def _check(fn: str, rc: int) -> None:
+    if rc != STTSM_OK:
+        raise SttsmError(fn, rc)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a) -> ctypes.c_void_p:
+    """Host buffer pointer: a CPU torch tensor or a numpy array."""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return DTYPE_F64
+    if t.dtype == torch.float32:
+        return DTYPE_F32
+    raise ValueError("BCSS tensors hold float64 or float32")
+
+
+# ---------------------------------------------------------------- BCSS indexing (host)
+
+def bcss_num_blocks(m: int, n: int, b: int) -> int:
+    return int(_load().bcss_num_blocks(m, n, b))
+
+
+def bcss_num_elems(m: int, n: int, b: int) -> int:
+    return int(_load().bcss_num_elems(m, n, b))
+
+
+def bcss_block_rank(sorted_blk_idx) -> int:
+    idx = list(sorted_blk_idx)
+    arr = (ctypes.c_int32 * len(idx))(*idx)
+    return int(_load().bcss_block_rank(len(idx), arr))
+
+
+def bcss_block_unrank(m: int, rank: int) -> tuple:
+    arr = (ctypes.c_int32 * m)()
+    _check("bcss_block_unrank", _load().bcss_block_unrank(m, rank, arr))
+    return tuple(arr)
+
+
+def sttsm_flops(m: int, n: int, p: int, b: int) -> float:
+    return float(_load().sttsm_flops(m, n, p, b))
+
+
+# ---------------------------------------------------------------- device calls
+
+def bcss_pack(dense, bcss, m: int, n: int, b: int, stream=None) -> None:
+    if dense.dtype != bcss.dtype:
+        raise ValueError("dense and bcss must have the same dtype")
+    if dense.numel() != n ** m or bcss.numel() != bcss_num_elems(m, n, b):
+        raise ValueError("size mismatch")
+    _check("bcss_pack", _load().bcss_pack(_dptr(dense), _dptr(bcss), m, n, b, _dtype_code(dense), _stream(stream)))
+
+
+def bcss_unpack(bcss, dense, m: int, n: int, b: int, stream=None) -> None:
+    if dense.dtype != bcss.dtype:
+        raise ValueError("dense and bcss must have the same dtype")
+    if dense.numel() != n ** m or bcss.numel() != bcss_num_elems(m, n, b):
+        raise ValueError("size mismatch")
+    _check("bcss_unpack", _load().bcss_unpack(_dptr(bcss), _dptr(dense), m, n, b, _dtype_code(dense), _stream(stream)))
+
+
+def sttsm_workspace_size(m: int, n: int, p: int, b: int, prec: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check("sttsm_workspace_size", _load().sttsm_workspace_size(m, n, p, b, prec, ctypes.byref(out)))
+    return int(out.value)
+
+
+def _check_operands(A, X, C, m, n, p, b, prec):
+    import torch
+    want = torch.float64 if prec == STTSM_FP64 else torch.float32
+    for name, t in (("A", A), ("X", X), ("C", C)):
+        if t.dtype != want:
+            raise ValueError("%s must be %s for precision %s" % (name, want, PREC_NAMES.get(prec, prec)))
+    if A.numel() != bcss_num_elems(m, n, b) or C.numel() != bcss_num_elems(m, p, b) or X.numel() != p * n:
+        raise ValueError("size mismatch")
+
+
+def sttsm_bcss(A, X, m: int, n: int, p: int, b: int, C, prec: int, workspace, stream=None) -> None:
+    """C := [A; X, ..., X] on BCSS.  X: p*n elements, column-major (chi_{j,i} at j + i*p)."""
+    _check_operands(A, X, C, m, n, p, b, prec)
+    ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None and workspace.numel() else ctypes.c_void_p(0)
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("sttsm_bcss", _load().sttsm_bcss(_dptr(A), _dptr(X), m, n, p, b, _dptr(C), prec, ws, nbytes,
+                                            _stream(stream)))
+
+
+def sttsm_bcss_host(A, X, m: int, n: int, p: int, b: int, C, prec: int, dA, dX, dC, workspace, stream=None) -> None:
+    """End-to-end call on host buffers A, X, C (pinned CPU tensors or numpy arrays)."""
+    ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None and workspace.numel() else ctypes.c_void_p(0)
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("sttsm_bcss_host", _load().sttsm_bcss_host(_hptr(A), _hptr(X), m, n, p, b, _hptr(C), prec,
+                                                      _dptr(dA), _dptr(dX), _dptr(dC), ws, nbytes, _stream(stream)))
+
+
+def sttsm_device_status() -> int:
+    return int(_load().sttsm_device_status())
+
+
+def sttsm_plan_level(m: int, n: int, p: int, b: int, prec: int, d: int):
+    """Level-d plan as numpy arrays: (tiles [ntiles x 8] int32, G [P_out x nbar] int32, info dict)."""
+    import numpy as np
+    L = _load()
+    nt, ng = ctypes.c_int64(0), ctypes.c_int64(0)
+    info = (ctypes.c_int64 * 9)()
+    _check("sttsm_plan_level", L.sttsm_plan_level(m, n, p, b, prec, d, None, 0, None, 0, ctypes.byref(nt),
+                                                  ctypes.byref(ng), info))
+    tiles = np.zeros((nt.value, 8), dtype=np.int32)
+    G = np.zeros(ng.value, dtype=np.int32)
+    _check("sttsm_plan_level", L.sttsm_plan_level(m, n, p, b, prec, d, tiles.ctypes.data, nt.value, G.ctypes.data,
+                                                  ng.value, None, None, info))
+    keys = ["k", "P_parent", "P_out", "rows_per_parent", "nodes_parent", "nodes_out", "R", "bm", "BM"]
+    return tiles, G, dict(zip(keys, [int(v) for v in info]))
+
+
+def workspace_tensor(m: int, n: int, p: int, b: int, prec: int, device=None):
+    """A uint8 CUDA tensor of sttsm_workspace_size bytes (torch allocations are 256-byte aligned)."""
+    import torch
+    return torch.empty(max(sttsm_workspace_size(m, n, p, b, prec), 1), dtype=torch.uint8,
+                       device=device if device is not None else "cuda")

@@ -1,0 +1,307 @@
+// capi.cu — C ABI of the sttsm library (declared in include/sttsm.h).
+#include <cudaTypedefs.h>
+#include <cstring>
+#include <mutex>
+#include <vector>
+#include "launch.h"
+#include "plan.h"
+#include "sttsm.h"
+
+using namespace sttsm;
+
+namespace {
+
+int* g_status_host = nullptr;   // host-mapped pinned status word
+int* g_status_dev = nullptr;
+std::mutex g_status_mu;
+
+int* status_dev()
+{
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    if (!g_status_host) {
+        if (cudaHostAlloc((void**)&g_status_host, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+            return nullptr;
+        *g_status_host = 0;
+        if (cudaHostGetDevicePointer((void**)&g_status_dev, g_status_host, 0) != cudaSuccess) return nullptr;
+    }
+    return g_status_dev;
+}
+
+int take_status()
+{
+    if (!g_status_host) return 0;
+    int v = __atomic_exchange_n(g_status_host, 0, __ATOMIC_SEQ_CST);
+    return v;
+}
+
+int num_sms()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    return v;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int npiece_of(int prec)
+{
+    if (prec == STTSM_BF16X6) return 3;
+    if (prec == STTSM_BF16X3) return 2;
+    return 0;
+}
+
+// Workspace layout: [X pieces (split precisions)][temporaries buffer 0][buffer 1].
+struct WsLayout {
+    size_t xpieces, buf0, buf1, total;
+    int rows, Kp;
+};
+
+WsLayout ws_layout(const Shape& s, int prec)
+{
+    WsLayout w;
+    const size_t esz = prec == STTSM_FP64 ? 8 : 4;
+    const int np = npiece_of(prec);
+    w.rows = (int)(s.pbar * s.b);
+    w.Kp = (int)(((s.nbar * s.b) + 7) / 8 * 8);
+    w.xpieces = 0;
+    size_t off = np ? align256((size_t)np * w.rows * w.Kp * 2) : 0;
+    w.buf0 = off;
+    off += align256((size_t)s.buf_elems[0] * esz);
+    w.buf1 = off;
+    off += align256((size_t)s.buf_elems[1] * esz);
+    w.total = off;
+    return w;
+}
+
+int cuda_err(int e) { return e == 0 ? STTSM_OK : STTSM_ERR_CUDA; }
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+}  // namespace
+
+namespace sttsm {
+
+int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp)
+{
+    auto enc = get_encode_fn();
+    if (!enc) return STTSM_ERR_CUDA;
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)npiece};
+    cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+    cuuint32_t box[3] = {(cuuint32_t)TC_KC, (cuuint32_t)TC_BN, (cuuint32_t)npiece};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(xpieces), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? STTSM_OK : STTSM_ERR_CUDA;
+}
+
+}  // namespace sttsm
+
+extern "C" {
+
+int64_t bcss_num_blocks(int m, int64_t n, int b)
+{
+    if (m < 1 || m > 64 || n < 1 || b < 1) return -1;
+    int64_t nbar = (n + b - 1) / b;
+    double c = 1.0;
+    for (int i = 1; i <= m; ++i) c = c * (double)(nbar - 1 + i) / i;
+    if (c > 9.0e18) return -1;
+    int64_t r = 1;
+    for (int i = 1; i <= m; ++i) r = r * (nbar - 1 + i) / i;
+    return r;
+}
+
+int64_t bcss_num_elems(int m, int64_t n, int b)
+{
+    int64_t nb = bcss_num_blocks(m, n, b);
+    if (nb < 0) return -1;
+    double e = (double)nb;
+    int64_t r = nb;
+    for (int a = 0; a < m; ++a) { e *= b; r *= b; }
+    if (e > 9.0e18) return -1;
+    return r;
+}
+
+int64_t bcss_block_rank(int m, const int32_t* s)
+{
+    if (m < 1 || m > STTSM_MAX_M || !s) return -1;
+    for (int a = 0; a < m; ++a) {
+        if (s[a] < 0 || (a > 0 && s[a] < s[a - 1])) return -1;
+    }
+    return colex_rank(s, m);
+}
+
+int bcss_block_unrank(int m, int64_t rank, int32_t* out)
+{
+    if (m < 1 || m > STTSM_MAX_M || rank < 0 || !out) return STTSM_ERR_ARG;
+    colex_unrank(rank, m, out);
+    return STTSM_OK;
+}
+
+double sttsm_flops(int m, int64_t n, int64_t p, int b)
+{
+    if (m < 1 || n < 1 || p < 1 || b < 1) return -1.0;
+    const double nbar = (double)((n + b - 1) / b), pbar = (double)((p + b - 1) / b);
+    auto C = [](double x, int y) {
+        if (y < 0 || x < y) return 0.0;
+        double c = 1.0;
+        for (int i = 1; i <= y; ++i) c = c * (x - y + i) / i;
+        return c;
+    };
+    double s = 0.0;
+    for (int d = 0; d < m; ++d) s += C(pbar + d, d + 1) * C(nbar + m - d - 2, m - d - 1);
+    double bp = 1.0;
+    for (int a = 0; a <= m; ++a) bp *= b;
+    return 2.0 * nbar * bp * s;
+}
+
+int bcss_pack(const void* dense, void* bcss, int m, int64_t n, int b, int dtype, void* stream)
+{
+    if (!dense || !bcss || m < 1 || m > STTSM_MAX_M || n < 1 || b < 1 || (dtype != 0 && dtype != 1)) return STTSM_ERR_ARG;
+    if (bcss_num_elems(m, n, b) < 0 || bcss_num_blocks(m, n, b) >= (int64_t)1 << 31) return STTSM_ERR_UNSUPPORTED;
+    return cuda_err(launch_bcss_pack(dense, bcss, m, n, b, dtype, (cudaStream_t)stream));
+}
+
+int bcss_unpack(const void* bcss, void* dense, int m, int64_t n, int b, int dtype, void* stream)
+{
+    if (!dense || !bcss || m < 1 || m > STTSM_MAX_M || n < 1 || b < 1 || (dtype != 0 && dtype != 1)) return STTSM_ERR_ARG;
+    if (bcss_num_elems(m, n, b) < 0) return STTSM_ERR_UNSUPPORTED;
+    return cuda_err(launch_bcss_unpack(bcss, dense, m, n, b, dtype, (cudaStream_t)stream));
+}
+
+int sttsm_workspace_size(int m, int64_t n, int64_t p, int b, int prec, size_t* bytes)
+{
+    if (!bytes) return STTSM_ERR_ARG;
+    if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
+    if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
+    Shape s;
+    int rc = make_shape(m, n, p, b, &s);
+    if (rc != STTSM_OK) return rc;
+    *bytes = ws_layout(s, prec).total;
+    return STTSM_OK;
+}
+
+int sttsm_device_status(void) { return take_status(); }
+
+int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_t* tiles, int64_t tiles_cap,
+                     int32_t* G, int64_t G_cap, int64_t* ntiles_out, int64_t* nG_out, int64_t* info)
+{
+    if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
+    if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
+    Shape s;
+    int rc = make_shape(m, n, p, b, &s);
+    if (rc != STTSM_OK) return rc;
+    if (d < 0 || d >= m) return STTSM_ERR_ARG;
+    const bool fp64 = prec == STTSM_FP64;
+    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : TC_BN;
+    std::vector<Tile> tl;
+    std::vector<int32_t> g;
+    build_level_tiles(s, d, BM, BN, 0, tl);
+    build_level_G(s, d, g);
+    if (ntiles_out) *ntiles_out = (int64_t)tl.size();
+    if (nG_out) *nG_out = (int64_t)g.size();
+    const LevelShape& L = s.lv[d];
+    if (info) {
+        int64_t v[9] = {L.k, L.P_parent, L.P_out, L.P_out * s.R, L.nodes_parent, L.nodes_out, s.R, s.bm, BM};
+        for (int i = 0; i < 9; ++i) info[i] = v[i];
+    }
+    if (tiles) {
+        if (tiles_cap < (int64_t)tl.size()) return STTSM_ERR_NOMEM;
+        memcpy(tiles, tl.data(), tl.size() * sizeof(Tile));
+    }
+    if (G) {
+        if (G_cap < (int64_t)g.size()) return STTSM_ERR_NOMEM;
+        memcpy(G, g.data(), g.size() * sizeof(int32_t));
+    }
+    return STTSM_OK;
+}
+
+int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b, void* C, int prec,
+               void* workspace, size_t ws_bytes, void* stream_)
+{
+    if (!A || !X || !C) return STTSM_ERR_ARG;
+    if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
+    if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
+    if (!aligned(A, 16) || !aligned(X, 16) || !aligned(C, 16)) return STTSM_ERR_ARG;
+    if (n >= (int64_t)1 << 30 || p >= (int64_t)1 << 30) return STTSM_ERR_UNSUPPORTED;
+    Shape s;
+    int rc = make_shape(m, n, p, b, &s);
+    if (rc != STTSM_OK) return rc;
+    const WsLayout w = ws_layout(s, prec);
+    if (w.total > 0 && (!workspace || ws_bytes < w.total || !aligned(workspace, 256))) return STTSM_ERR_NOMEM;
+    int* st = status_dev();
+    if (!st) return STTSM_ERR_CUDA;
+    if (take_status() != 0) return STTSM_ERR_TIMEOUT;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const bool fp64 = prec == STTSM_FP64;
+    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : TC_BN;
+    const DevPlan* P = get_dev_plan(m, n, p, b, BM, BN);
+    if (!P) return STTSM_ERR_NOMEM;
+    char* ws = (char*)workspace;
+    void* bufs[2] = {ws + w.buf0, ws + w.buf1};
+    const int sms = num_sms();
+    const int np = npiece_of(prec);
+    TcInst ti;
+    memset(&ti, 0, sizeof(ti));
+    if (!fp64) {
+        rc = cuda_err(launch_split_x((const float*)X, ws + w.xpieces, (int)p, (int)n, w.rows, w.Kp, np, stream));
+        if (rc != STTSM_OK) return rc;
+        rc = make_x_tensor_map(&ti.tmX, ws + w.xpieces, np, w.rows, w.Kp);
+        if (rc != STTSM_OK) return rc;
+    }
+    for (int d = 0; d < m; ++d) {
+        const LevelShape& LS = s.lv[d];
+        LevelInst& L = ti.L;
+        L.parent = d == 0 ? A : bufs[(d - 1) & 1];
+        L.out = d == m - 1 ? C : bufs[d & 1];
+        L.G = P->d_G[d];
+        L.X = X;
+        L.m = m; L.b = b; L.k = LS.k; L.nbar = (int32_t)s.nbar;
+        L.n = (int32_t)n; L.p = (int32_t)p;
+        L.R = (int32_t)s.R;
+        L.Ktot = (int32_t)(s.nbar * b);
+        L.bm = s.bm;
+        L.P_parent = LS.P_parent;
+        L.P_out = LS.P_out;
+        L.rows_per_parent = LS.P_out * s.R;
+        int64_t bp = 1;
+        for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
+        if (fp64) rc = cuda_err(launch_level_fp64(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
+        else rc = cuda_err(launch_level_tc(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
+        if (rc != STTSM_OK) return rc;
+    }
+    return STTSM_OK;
+}
+
+int sttsm_bcss_host(const void* A, const void* X, int m, int64_t n, int64_t p, int b, void* C, int prec,
+                    void* dA, void* dX, void* dC, void* workspace, size_t ws_bytes, void* stream_)
+{
+    if (!A || !X || !C || !dA || !dX || !dC) return STTSM_ERR_ARG;
+    const size_t esz = prec == STTSM_FP64 ? 8 : 4;
+    const int64_t na = bcss_num_elems(m, n, b), nc = bcss_num_elems(m, p, b);
+    if (na < 0 || nc < 0) return STTSM_ERR_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (cudaMemcpyAsync(dA, A, (size_t)na * esz, cudaMemcpyHostToDevice, stream) != cudaSuccess) return STTSM_ERR_CUDA;
+    if (cudaMemcpyAsync(dX, X, (size_t)(p * n) * esz, cudaMemcpyHostToDevice, stream) != cudaSuccess) return STTSM_ERR_CUDA;
+    int rc = sttsm_bcss(dA, dX, m, n, p, b, dC, prec, workspace, ws_bytes, stream_);
+    if (rc != STTSM_OK) return rc;
+    if (cudaMemcpyAsync(C, dC, (size_t)nc * esz, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return STTSM_ERR_CUDA;
+    return STTSM_OK;
+}
+
+}  // extern "C"

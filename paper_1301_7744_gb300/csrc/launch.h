@@ -1,0 +1,35 @@
+// launch.h — internal host-side launchers of the sttsm kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace sttsm {
+
+// Split-precision level launch: per-instance data plus the TMA descriptor of
+// that instance's X pieces ([npiece][rows][Kp] BF16, K-major rows).
+struct TcInst {   // CUtensorMap first: inherits its 64-byte alignment
+    CUtensorMap tmX;
+    LevelInst L;
+};
+
+int launch_bcss_pack(const void* dense, void* bcss, int m, int64_t n, int b, int dtype, cudaStream_t s);
+int launch_bcss_unpack(const void* bcss, void* dense, int m, int64_t n, int b, int dtype, cudaStream_t s);
+int launch_split_x(const float* X, void* out, int p, int n, int rows, int Kp, int npiece, cudaStream_t s);
+int launch_level_fp64(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
+                      int num_sms, cudaStream_t s);
+
+// Tensor-core level launch (tcgen05, BF16 pieces, FP32 accumulation in TMEM).
+// Tiles are 128 rows x up to TC_BN columns.  Either inst0 (single instance,
+// d_insts == nullptr) or d_insts[tile.inst] describes each tile.
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 256;
+constexpr int TC_KC = 32;
+int launch_level_tc(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
+                    int num_sms, int* d_status, cudaStream_t s);
+
+// Builds the TMA descriptor of an X-piece array.
+int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp);
+
+}  // namespace sttsm

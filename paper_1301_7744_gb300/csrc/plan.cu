@@ -1,0 +1,147 @@
+// plan.cu — host-side level plans (see plan.h).
+#include <map>
+#include <mutex>
+#include <tuple>
+#include "plan.h"
+#include "sttsm.h"
+
+namespace sttsm {
+
+int make_shape(int m, int64_t n, int64_t p, int b, Shape* s)
+{
+    if (m < 1 || n < 1 || p < 1 || b < 1) return STTSM_ERR_ARG;
+    if (m > STTSM_MAX_M) return STTSM_ERR_UNSUPPORTED;
+    s->m = m; s->b = b; s->n = n; s->p = p;
+    s->nbar = (n + b - 1) / b;
+    s->pbar = (p + b - 1) / b;
+    double bmd = 1.0;
+    for (int a = 0; a < m; ++a) bmd *= b;
+    if (bmd / b >= 2147483647.0 || bmd > 1.0e12) return STTSM_ERR_UNSUPPORTED;   // b^(m-1) must fit int32
+    s->bm = 1;
+    for (int a = 0; a < m; ++a) s->bm *= b;
+    s->R = s->bm / b;
+    // every block count below must stay below 2^27 (ranks are packed with q)
+    auto safe_binom = [](int64_t x, int y) -> int64_t {
+        double c = 1.0;
+        for (int i = 1; i <= y; ++i) c = c * (double)(x - y + i) / i;
+        if (x < y) return 0;
+        if (c >= 134217728.0) return -1;
+        return binom_small(x, y);
+    };
+    s->buf_elems[0] = s->buf_elems[1] = 0;
+    for (int d = 0; d < m; ++d) {
+        LevelShape& L = s->lv[d];
+        L.d = d;
+        L.k = m - 1 - d;
+        L.nodes_parent = d == 0 ? 1 : safe_binom(s->pbar + d - 1, d);
+        L.nodes_out = safe_binom(s->pbar + d, d + 1);
+        L.P_parent = safe_binom(s->nbar + L.k, L.k + 1);
+        L.P_out = L.k == 0 ? 1 : safe_binom(s->nbar + L.k - 1, L.k);
+        if (L.nodes_parent < 0 || L.nodes_out < 0 || L.P_parent < 0 || L.P_out < 0) return STTSM_ERR_UNSUPPORTED;
+        if ((double)L.P_out * (double)s->R >= 2147483647.0) return STTSM_ERR_UNSUPPORTED;
+        if (d < m - 1) {
+            int64_t e = L.nodes_out * L.P_out * s->bm;
+            if (e > s->buf_elems[d & 1]) s->buf_elems[d & 1] = e;
+        }
+    }
+    return STTSM_OK;
+}
+
+void build_level_G(const Shape& s, int d, std::vector<int32_t>& G)
+{
+    const LevelShape& L = s.lv[d];
+    const int k = L.k;
+    G.resize((size_t)(L.P_out * s.nbar));
+    int32_t prefix[STTSM_MAX_M], stored[STTSM_MAX_M];
+    for (int64_t pr = 0; pr < L.P_out; ++pr) {
+        if (k > 0) colex_unrank(pr, k, prefix);
+        for (int64_t ib = 0; ib < s.nbar; ++ib) {
+            // insert ib before the first prefix entry >= ib; q = its position
+            int q = 0;
+            while (q < k && prefix[q] < ib) ++q;
+            for (int t = 0; t < q; ++t) stored[t] = prefix[t];
+            stored[q] = (int32_t)ib;
+            for (int t = q; t < k; ++t) stored[t + 1] = prefix[t];
+            const int64_t rank = colex_rank(stored, k + 1);
+            G[(size_t)(pr * s.nbar + ib)] = (int32_t)((rank << 3) | q);
+        }
+    }
+}
+
+void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles)
+{
+    const LevelShape& L = s.lv[d];
+    const int64_t rows = L.P_out * s.R;
+    int32_t u[STTSM_MAX_M];
+    for (int64_t par = 0; par < L.nodes_parent; ++par) {
+        int64_t children, child_base = 0;
+        if (d == 0) {
+            children = s.pbar;
+        } else {
+            colex_unrank(par, d, u);   // parent (jbar_{k+1} <= ... <= jbar_{m-1})
+            children = (int64_t)u[0] + 1;
+            for (int t = 0; t < d; ++t) child_base += binom_small((int64_t)u[t] + t + 1, t + 2);
+        }
+        const int64_t ncols = children * s.b;
+        for (int64_t r0 = 0; r0 < rows; r0 += BM) {
+            for (int64_t c0 = 0; c0 < ncols; c0 += BN) {
+                Tile t;
+                t.inst = inst;
+                t.parent = (int32_t)par;
+                t.child_base = (int32_t)child_base;
+                t.row0 = (int32_t)r0;
+                t.col0 = (int32_t)c0;
+                t.ncols = (int32_t)(ncols - c0 < BN ? ncols - c0 : BN);
+                t.pad0 = t.pad1 = 0;
+                tiles.push_back(t);
+            }
+        }
+    }
+}
+
+namespace {
+std::mutex g_mu;
+std::map<std::tuple<int, int, int64_t, int64_t, int, int, int>, DevPlan*> g_plans;
+
+void free_plan(DevPlan* P)
+{
+    for (int d = 0; d < STTSM_MAX_M; ++d) {
+        if (P->d_tiles[d]) cudaFree(P->d_tiles[d]);
+        if (P->d_G[d]) cudaFree(P->d_G[d]);
+    }
+    delete P;
+}
+}  // namespace
+
+const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    auto key = std::make_tuple(dev, m, n, p, b, BM, BN);
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) return it->second;
+    DevPlan* P = new DevPlan();
+    for (int d = 0; d < STTSM_MAX_M; ++d) { P->d_tiles[d] = nullptr; P->d_G[d] = nullptr; P->ntiles[d] = 0; }
+    if (make_shape(m, n, p, b, &P->shape) != STTSM_OK) { delete P; return nullptr; }
+    P->BM = BM;
+    P->BN = BN;
+    for (int d = 0; d < m; ++d) {
+        std::vector<Tile> tiles;
+        std::vector<int32_t> G;
+        build_level_tiles(P->shape, d, BM, BN, 0, tiles);
+        build_level_G(P->shape, d, G);
+        P->ntiles[d] = (int)tiles.size();
+        if (cudaMalloc(&P->d_tiles[d], tiles.size() * sizeof(Tile)) != cudaSuccess ||
+            cudaMalloc(&P->d_G[d], G.size() * sizeof(int32_t)) != cudaSuccess ||
+            cudaMemcpy(P->d_tiles[d], tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(P->d_G[d], G.data(), G.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+            free_plan(P);
+            return nullptr;
+        }
+    }
+    g_plans[key] = P;
+    return P;
+}
+
+}  // namespace sttsm

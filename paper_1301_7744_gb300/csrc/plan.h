@@ -1,0 +1,52 @@
+// plan.h — host-side plans of the algorithm-by-blocks (Fig. 5 with Thm. 1):
+// per level, the parent nodes, the unique output blocks, the gather table G
+// and the tile list; cached per shape in library-owned device memory.
+#pragma once
+
+#include <stdint.h>
+#include <vector>
+#include "common.cuh"
+
+namespace sttsm {
+
+struct LevelShape {
+    int d, k;                  // level d writes T^(k), k = m-1-d
+    int64_t nodes_parent;      // C(pbar+d-1, d) parent nodes (1 at level 0)
+    int64_t nodes_out;         // C(pbar+d, d+1) child nodes
+    int64_t P_parent;          // unique blocks per parent node: C(nbar+k, k+1)
+    int64_t P_out;             // unique blocks per child node: C(nbar+k-1, k) (1 if k = 0)
+};
+
+// Shape facts of one sttsm instance (host only, no allocation).
+struct Shape {
+    int m, b;
+    int64_t n, p, nbar, pbar;
+    int64_t bm;                // b^m
+    int64_t R;                 // b^(m-1)
+    LevelShape lv[STTSM_MAX_M];
+    int64_t buf_elems[2];      // ping-pong temporaries (elements)
+};
+
+// Returns 0 and fills s, or an sttsm_status for unsupported sizes.
+int make_shape(int m, int64_t n, int64_t p, int b, Shape* s);
+
+// Host tile list and G table of level d (appended to the given vectors).
+// Tiles cover, for every parent node, P_out * R rows in steps of BM and the
+// parent's children * b columns in steps of BN.
+void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles);
+void build_level_G(const Shape& s, int d, std::vector<int32_t>& G);
+
+struct DevPlan {
+    Shape shape;
+    int BM, BN;
+    int ntiles[STTSM_MAX_M];
+    Tile* d_tiles[STTSM_MAX_M];
+    int32_t* d_G[STTSM_MAX_M];
+};
+
+// Cached device plan for (shape, tile sizes) on the current device; nullptr
+// on allocation failure.  Thread-safe.  The first call for a shape allocates
+// and copies synchronously (do it before any stream capture).
+const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN);
+
+}  // namespace sttsm

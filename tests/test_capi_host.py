@@ -1,0 +1,100 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports
+every entry point the header declares, and its BCSS indexing and cost model
+agree with the oracle's independent enumeration."""
+import itertools
+import math
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def st():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_7744_gb300 as pkg
+    pkg._load()
+    return pkg
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted((ROOT / "include").glob("*.h")):
+        text = re.sub(r"/\*.*?\*/", "", hdr.read_text(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:int64_t|int|double|void)\s+\**(\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol(st):
+    import ctypes
+    lib = ctypes.CDLL(str(st.lib_path()))
+    names = declared_functions()
+    assert "sttsm_bcss" in names and "bcss_pack" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(st.exported_symbols()) <= set(names)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6])
+def test_block_counts(st, m):
+    for n, b in [(24, 8), (25, 8), (7, 3), (16, 16), (5, 1)]:
+        nbar = -(-n // b)
+        assert st.bcss_num_blocks(m, n, b) == oracle.bcss_count_blocks(m, nbar)
+        assert st.bcss_num_elems(m, n, b) == b ** m * oracle.bcss_count_blocks(m, nbar)
+
+
+@pytest.mark.parametrize("m,nbar", [(1, 6), (2, 5), (3, 5), (4, 4), (5, 3), (6, 3)])
+def test_rank_matches_oracle_storage_order(st, m, nbar):
+    """With b = 1 the oracle's BCSS storage order is the order of the stored
+    tuples; encode each entry by its sorted tuple and compare with unrank."""
+    n = nbar
+    dense = np.empty(n ** m)
+    for lin in range(n ** m):
+        idx = sorted(np.unravel_index(lin, (n,) * m, order="F"))
+        dense[lin] = sum(int(v) * (n + 1) ** a for a, v in enumerate(idx))
+    packed = oracle.bcss_pack(dense, m, n, 1)
+    for r, code in enumerate(packed):
+        tup = []
+        c = int(code)
+        for _ in range(m):
+            tup.append(c % (n + 1))
+            c //= n + 1
+        assert st.bcss_block_unrank(m, r) == tuple(tup)
+        assert st.bcss_block_rank(tup) == r
+
+
+def test_rank_rejects_unsorted(st):
+    assert st.bcss_block_rank([2, 1, 3]) == -1
+    assert st.bcss_block_rank([-1, 0]) == -1
+
+
+@pytest.mark.parametrize("m,n,p,b", [(3, 24, 24, 8), (3, 768, 768, 64), (3, 768, 768, 32), (3, 768, 768, 48),
+                                     (4, 128, 64, 8), (4, 128, 64, 16), (4, 128, 64, 32), (5, 37, 20, 4), (2, 9, 11, 3),
+                                     (1, 10, 7, 4), (6, 20, 12, 8)])
+def test_flops_match_oracle_count(st, m, n, p, b):
+    assert st.sttsm_flops(m, n, p, b) == pytest.approx(oracle.bcss_flops(m, n, p, b), rel=1e-13)
+
+
+def test_workspace_sizes(st):
+    # FP64 needs the two temporaries buffers; split precisions add X pieces
+    ws64 = st.sttsm_workspace_size(3, 24, 24, 8, st.STTSM_FP64)
+    ws32 = st.sttsm_workspace_size(3, 24, 24, 8, st.STTSM_BF16X6)
+    # level 0 output: C(pbar,1) nodes * C(nbar+1,2) blocks * b^3 ; level 1: C(pbar+1,2) * nbar * b^3
+    l0 = 3 * 6 * 512
+    l1 = 6 * 3 * 512
+    assert ws64 >= 8 * (l0 + l1)
+    assert ws32 >= 4 * (l0 + l1) + 3 * 24 * 24 * 2
+    with pytest.raises(st.SttsmError) as e:
+        st.sttsm_workspace_size(3, 24, 24, 8, st.STTSM_TF32X3)
+    assert e.value.code == st.STTSM_ERR_UNSUPPORTED
+    with pytest.raises(st.SttsmError):
+        st.sttsm_workspace_size(9, 24, 24, 8, st.STTSM_FP64)
+    with pytest.raises(st.SttsmError):
+        st.sttsm_workspace_size(3, 0, 24, 8, st.STTSM_FP64)
