@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Throughput of sttsm, C := [A; X, X, X], on the large single-instance workload.
+
+Workload: m = 3, n = p = 768, A symmetric Uniform(-1,1) in BCSS (FP32),
+X N(0, 1/n) (FP32), block size b from {32, 48, 64} (chosen by a short
+measurement unless --b is given), BF16X6 split-precision tensor-core path.
+A step is one sttsm_bcss call: the X split plus the m level launches of the
+algorithm-by-blocks.  Useful flops are the paper's BCSS count (Tbl. 4,
+MinCosts) — `sttsm_flops`.  Inputs (A: >= 340 MB) are larger than the 129 MB
+L2, so no flush is needed between steps.
+
+Also reported: the plain FP64 GPU path on the same workload, the sampled
+relative error of both paths against the FP64 oracle, an end-to-end figure
+through the host-buffer entry point (H2D of A and X, D2H of C inside the
+timed region), the roofline of the dominant kernel from CUDA events the
+library records on its launch stream, SM clocks sampled during the timed
+region, and the FP64 CPU oracle timed on this host (cpu_baseline).
+
+Multi-GPU (torchrun): every rank runs its own independent instance
+(replicas, weak scaling); value = all ranks' useful flops / max time.
+
+`--impl reference` times the FP64 CPU oracle (the dense successive
+mode-product chain) on bounded slices of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sttsm TFLOP/s (paper's BCSS flop count) & % peak, BF16x3 vs FP64 at stated rel err; p99 ms"
+M, N, P = 3, 768, 768
+SEED_A, SEED_X, SEED_J = 0, 1, 2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--b", default="auto", help="block size or 'auto'")
+    ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3"])
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle error check and CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            if vis and "," not in vis:
+                cmd += ["-i", vis]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        first = rows[0][0]
+        rows = [r for r in rows if r[0] == first]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------- inputs
+
+def xcol32(X):
+    return np.asfortranarray(X).reshape(-1, order="F").astype(np.float32)
+
+
+def make_device_inputs(st, torch, b, dtype):
+    import synth
+    dense = torch.empty(N ** M, dtype=dtype, device="cuda")
+    synth.dev_sym_uniform_dense(dense.data_ptr(), M, N, SEED_A, "f64" if dtype == torch.float64 else "f32",
+                                torch.cuda.current_stream().cuda_stream)
+    A = torch.empty(st.bcss_num_elems(M, N, b), dtype=dtype, device="cuda")
+    st.bcss_pack(dense, A, M, N, b)
+    torch.cuda.synchronize()
+    del dense
+    torch.cuda.empty_cache()
+    return A
+
+
+def bcss_pos(j, b):
+    import math
+    s = sorted(int(x) for x in j)
+    rank = sum(math.comb(s[t] // b + t, t + 1) for t in range(M))
+    return rank * b ** M + sum((s[t] % b) * b ** t for t in range(M))
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline)
+
+def oracle_slice_rate(A_dense, X, target_s, max_slices=None):
+    """Times the oracle's dense mode-product chain on S slices C[:, :, j] (j a
+    seeded sample of rows of X for the last mode), S sized from one timed
+    slice to take about target_s seconds; returns (seconds, S)."""
+    import oracle
+    rng = np.random.default_rng(SEED_J)
+    t0 = time.perf_counter()
+    oracle.ttm_chain(A_dense, [X, X, X[rng.integers(0, P, size=1)]], M)
+    one = time.perf_counter() - t0
+    S = max(1, int(target_s / max(one, 1e-3)))
+    if max_slices:
+        S = min(S, max_slices)
+    rows = rng.integers(0, P, size=S)
+    t0 = time.perf_counter()
+    oracle.ttm_chain(A_dense, [X, X, X[rows]], M)
+    dt = time.perf_counter() - t0
+    return dt, S
+
+
+def cpu_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import synth
+    import oracle
+    b = 64 if args.b == "auto" else int(args.b)
+    F = bcss_flops_host(b)
+    A = synth.sym_uniform_dense(M, N, SEED_A)
+    X = synth.x_gaussian(SEED_X, P, N).astype(np.float32).astype(np.float64)
+    oracle.build()
+    per_step = max(2.0, min(10.0, 120.0 / max(1, args.steps + args.warmup)))
+    _, S = oracle_slice_rate(A, X, per_step)
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt = _timed_slices(A, X, S, i)
+        if i >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    value = F * S / P / t / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sttsm m=3 n=p=768 b=%d" % b, "m": M, "n": N, "p": P, "b": b},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": "FP64 oracle dense mode-product chain on %d of %d slices C[:,:,j] per step; "
+                                       "value scales the BCSS flop count by %d/%d" % (S, P, S, P)},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _timed_slices(A, X, S, i):
+    import oracle
+    rng = np.random.default_rng(SEED_J + 1 + i)
+    rows = rng.integers(0, P, size=S)
+    t0 = time.perf_counter()
+    oracle.ttm_chain(A, [X, X, X[rows]], M)
+    return time.perf_counter() - t0
+
+
+def bcss_flops_host(b):
+    """Tbl. 4 (MinCosts) BCSS flop count, restated for the reference leg (no library load)."""
+    import math
+    nbar, pbar = -(-N // b), -(-P // b)
+    s = sum(math.comb(pbar + d, d + 1) * math.comb(nbar + M - d - 2, M - d - 1) for d in range(M))
+    return 2.0 * nbar * b ** (M + 1) * s
+
+
+# ---------------------------------------------------------------- our arm
+
+def time_steps(torch, fn, steps, warmup, per_step_events=True):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record()
+    for i in range(steps):
+        ev[i][0].record()
+        fn()
+        ev[i][1].record()
+    t_all1.record()
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b_) for a, b_ in ev]
+    return t_all0.elapsed_time(t_all1), per
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.init_process_group("nccl")
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()
+    torch.cuda.set_device(local)
+    import paper_1301_7744_gb300 as st
+
+    prec = st.STTSM_BF16X6 if args.prec == "bf16x6" else st.STTSM_BF16X3
+    import synth
+    Xh = synth.x_gaussian(SEED_X, P, N)
+    X32 = Xh.astype(np.float32).astype(np.float64)
+    dX = torch.from_numpy(xcol32(Xh)).cuda()
+
+    # ---- block size: short measurement over {32, 48, 64}
+    sweep = {}
+    cands = [32, 48, 64] if args.b == "auto" else [int(args.b)]
+    for b in cands:
+        A = make_device_inputs(st, torch, b, torch.float32)
+        C = torch.empty(st.bcss_num_elems(M, P, b), dtype=torch.float32, device="cuda")
+        ws = st.workspace_tensor(M, N, P, b, prec)
+        if len(cands) > 1:
+            tot, _ = time_steps(torch, lambda: st.sttsm_bcss(A, dX, M, N, P, b, C, prec, ws), 3, 2)
+            sweep[b] = st.sttsm_flops(M, N, P, b) / (tot / 3 * 1e-3) / 1e12
+        del A, C, ws
+        torch.cuda.empty_cache()
+    b = max(sweep, key=sweep.get) if sweep else cands[0]
+    F = st.sttsm_flops(M, N, P, b)
+
+    A = make_device_inputs(st, torch, b, torch.float32)
+    C = torch.empty(st.bcss_num_elems(M, P, b), dtype=torch.float32, device="cuda")
+    ws = st.workspace_tensor(M, N, P, b, prec)
+
+    def step():
+        st.sttsm_bcss(A, dX, M, N, P, b, C, prec, ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    st.sttsm_profile_enable(True)
+    total_ms, per = time_steps(torch, step, args.steps, 0)
+    st.sttsm_profile_enable(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms = total_ms / args.steps
+    value = F * world / (ms * 1e-3) / 1e12
+
+    # ---- dominant kernel roofline from the library's per-launch events
+    recs = st.sttsm_profile_read()
+    tc = [r for r in recs if r["kind"] == "tc"]
+    kern_ms = sum(r["ms"] for r in tc)
+    kern_flops = sum(r["useful_flops"] for r in tc)
+    nprod = 6 if prec == st.STTSM_BF16X6 else 3
+    pk, pk_src = peaks()
+    mma_tflops = kern_flops * nprod / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else 0.0
+    peak = float(pk.get("bf16_tflops_sustained", 1700.0))
+    per_level = {}
+    for r in tc:
+        d = per_level.setdefault(r["level"], {"ms": 0.0, "flops": 0.0, "n": 0})
+        d["ms"] += r["ms"]
+        d["flops"] += r["useful_flops"]
+        d["n"] += 1
+    levels = {str(k): {"ms_per_launch": v["ms"] / v["n"],
+                       "useful_tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12,
+                       "mma_frac_of_peak": v["flops"] * nprod / (v["ms"] * 1e-3) / 1e12 / peak}
+              for k, v in sorted(per_level.items())}
+    roofline = {"bound": "tensor", "achieved": mma_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": mma_tflops / peak, "traffic": None,
+                "kernel": "level_tc_kernel<3> (all levels)",
+                "achieved_counts": "useful flops x %d piece products per launch / CUDA-event duration" % nprod,
+                "peak_source": "bf16_tflops_sustained of %s MEASURED_PEAKS" % pk_src,
+                "useful_tflops": kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else 0.0,
+                "kernel_share_of_step": kern_ms / total_ms if total_ms > 0 else None,
+                "levels": levels}
+
+    # ---- end to end through the host-buffer entry point
+    hA = A.cpu().pin_memory()
+    hX = torch.from_numpy(xcol32(Xh)).pin_memory()
+    hC = torch.empty(C.numel(), dtype=torch.float32).pin_memory()
+    dA2, dX2, dC2 = torch.empty_like(A), torch.empty_like(dX), torch.empty_like(C)
+
+    def e2e_step():
+        st.sttsm_bcss_host(hA, hX, M, N, P, b, hC, prec, dA2, dX2, dC2, ws)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(2):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e = {"value": F / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(hA.numel() * 4 + hX.numel() * 4), "d2h_bytes_per_step": int(hC.numel() * 4),
+           "timer": "host wall clock around sttsm_bcss_host + stream sync"}
+    assert np.array_equal(hC.numpy(), C.cpu().numpy())
+    del hA, dA2, dC2
+
+    # ---- plain FP64 GPU path on the same workload
+    fp64 = None
+    if rank == 0:
+        A64 = make_device_inputs(st, torch, b, torch.float64)
+        dX64 = torch.from_numpy(np.asfortranarray(Xh).reshape(-1, order="F").copy()).cuda()
+        C64 = torch.empty(st.bcss_num_elems(M, P, b), dtype=torch.float64, device="cuda")
+        ws64 = st.workspace_tensor(M, N, P, b, st.STTSM_FP64)
+        tot64, _ = time_steps(torch, lambda: st.sttsm_bcss(A64, dX64, M, N, P, b, C64, st.STTSM_FP64, ws64), 2, 1)
+        ms64 = tot64 / 2
+        fp64 = {"value": F / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
+                "speedup_of_split_path": (F / (ms * 1e-3) / 1e12) / (F / (ms64 * 1e-3) / 1e12)}
+
+    # ---- accuracy against the oracle and the CPU baseline (rank 0, N = 1)
+    rel_err = None
+    cpu_base = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        oracle.build()
+        A_dense = synth.sym_uniform_dense(M, N, SEED_A)
+        J = np.sort(np.random.default_rng(SEED_J).integers(0, P, size=(256, M)), axis=1)
+        ref32 = oracle.sttsm_entries(A_dense, X32, M, J)
+        ref64 = oracle.sttsm_entries(A_dense, Xh, M, J)
+        c32 = C.double().cpu().numpy()
+        got32 = np.array([c32[bcss_pos(j, b)] for j in J])
+        rel_err = {"samples": 256, args.prec: float(np.linalg.norm(got32 - ref32) / np.linalg.norm(ref32)),
+                   "tolerance": {args.prec: 1e-6, "fp64": 1e-12}}
+        if fp64 is not None:
+            c64 = C64.cpu().numpy()
+            got64 = np.array([c64[bcss_pos(j, b)] for j in J])
+            rel_err["fp64"] = float(np.linalg.norm(got64 - ref64) / np.linalg.norm(ref64))
+        if world == 1:
+            dt, S = oracle_slice_rate(A_dense, X32, args.cpu_seconds)
+            cpu_base = {"value": F * S / P / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_threads(), "kind": "oracle",
+                        "sample": "FP64 oracle dense mode-product chain (A x_2 X_S x_1 X x_0 X) for %d of %d "
+                                  "slices C[:,:,j], %.1f s; value = BCSS flop count x %d/%d / time" % (S, P, dt, S, P)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "p99_ms_per_step": float(np.percentile(per, 99)),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+                "data": "synthetic",
+                "config": {"workload": "sttsm m=3 n=p=768 b=%d %s" % (b, args.prec.upper()), "m": M, "n": N, "p": P,
+                           "b": b, "precision": args.prec, "b_sweep_tflops": {str(k): v for k, v in sweep.items()},
+                           "useful_flops_per_step": F, "l2": "inputs larger than L2 (A in BCSS FP32: %.0f MB)"
+                           % (A.numel() * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e, "fp64_path": fp64, "rel_err": rel_err,
+                "gpu_launches": args.steps * (1 + M), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

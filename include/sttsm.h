@@ -156,6 +156,16 @@ int sttsm_device_status(void);
 int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_t* tiles, int64_t tiles_cap,
                      int32_t* G, int64_t G_cap, int64_t* ntiles_out, int64_t* nG_out, int64_t* info);
 
+/* Per-launch timing of the library's kernels (diagnostics).  While enabled,
+ * every kernel sttsm_bcss launches is bracketed by CUDA events on its
+ * stream.  sttsm_profile_enable(1) clears earlier records; (0) stops.
+ * sttsm_profile_read waits for the recorded events and copies up to `max`
+ * records: kind (0 = FP64 level, 1 = tensor-core level, 2 = X split),
+ * level d, useful flops of that launch (Tbl. 4 terms of level d; 0 for the
+ * split), and its duration in ms.  *count receives the number of records. */
+int sttsm_profile_enable(int on);
+int sttsm_profile_read(int max, int* kind, int* level, double* useful_flops, float* ms, int* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,10 @@ def _load():
     L.sttsm_bcss_host.restype = i32
     L.sttsm_device_status.argtypes = []
     L.sttsm_device_status.restype = i32
+    L.sttsm_profile_enable.argtypes = [i32]
+    L.sttsm_profile_enable.restype = i32
+    L.sttsm_profile_read.argtypes = [i32, P, P, P, P, P]
+    L.sttsm_profile_read.restype = i32
     L.sttsm_plan_level.argtypes = [i32, i64, i64, i32, i32, i32, P, i64, P, i64, P, P, P]
     L.sttsm_plan_level.restype = i32
     _lib = L
@@ -91,7 +95,7 @@ def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points this binding loads."""
     return ["bcss_num_blocks", "bcss_num_elems", "bcss_block_rank", "bcss_block_unrank", "sttsm_flops",
             "bcss_pack", "bcss_unpack", "sttsm_workspace_size", "sttsm_bcss", "sttsm_bcss_host",
-            "sttsm_device_status", "sttsm_plan_level"]
+            "sttsm_device_status", "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read"]
 
 
 def _check(fn: str, rc: int) -> None:
@@ -229,6 +233,28 @@ def sttsm_plan_level(m: int, n: int, p: int, b: int, prec: int, d: int):
                                                   ng.value, None, None, info))
     keys = ["k", "P_parent", "P_out", "rows_per_parent", "nodes_parent", "nodes_out", "R", "bm", "BM"]
     return tiles, G, dict(zip(keys, [int(v) for v in info]))
+
+
+def sttsm_profile_enable(on: bool) -> None:
+    _check("sttsm_profile_enable", _load().sttsm_profile_enable(1 if on else 0))
+
+
+def sttsm_profile_read() -> list[dict]:
+    """Recorded launches: dicts with kind ('fp64' | 'tc' | 'split'), level, useful_flops, ms."""
+    import numpy as np
+    L = _load()
+    cnt = ctypes.c_int(0)
+    _check("sttsm_profile_read", L.sttsm_profile_read(0, None, None, None, None, ctypes.byref(cnt)))
+    n = cnt.value
+    kind = np.zeros(n, dtype=np.int32)
+    level = np.zeros(n, dtype=np.int32)
+    flops = np.zeros(n, dtype=np.float64)
+    ms = np.zeros(n, dtype=np.float32)
+    _check("sttsm_profile_read", L.sttsm_profile_read(n, kind.ctypes.data, level.ctypes.data, flops.ctypes.data,
+                                                      ms.ctypes.data, ctypes.byref(cnt)))
+    names = {0: "fp64", 1: "tc", 2: "split"}
+    return [dict(kind=names[int(k)], level=int(l), useful_flops=float(f), ms=float(t))
+            for k, l, f, t in zip(kind, level, flops, ms)]
 
 
 def workspace_tensor(m: int, n: int, p: int, b: int, prec: int, device=None):

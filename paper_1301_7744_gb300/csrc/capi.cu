@@ -42,6 +42,45 @@ int num_sms()
     return v;
 }
 
+// ---- per-launch event timing (sttsm_profile_*)
+struct ProfRec {
+    cudaEvent_t a, b;
+    int kind, level;
+    double flops;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+
+struct ProfScope {
+    cudaStream_t s;
+    ProfRec r;
+    bool on;
+    ProfScope(cudaStream_t s_, int kind, int level, double flops) : s(s_), on(false)
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        if (!g_prof_on) return;
+        r.kind = kind; r.level = level; r.flops = flops;
+        if (cudaEventCreate(&r.a) != cudaSuccess) return;
+        if (cudaEventCreate(&r.b) != cudaSuccess) { cudaEventDestroy(r.a); return; }
+        cudaEventRecord(r.a, s);
+        on = true;
+    }
+    ~ProfScope()
+    {
+        if (!on) return;
+        cudaEventRecord(r.b, s);
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        g_prof.push_back(r);
+    }
+};
+
+void prof_clear_locked()
+{
+    for (auto& r : g_prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    g_prof.clear();
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
@@ -198,6 +237,31 @@ int sttsm_workspace_size(int m, int64_t n, int64_t p, int b, int prec, size_t* b
 
 int sttsm_device_status(void) { return take_status(); }
 
+int sttsm_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    if (on) prof_clear_locked();
+    g_prof_on = on != 0;
+    return STTSM_OK;
+}
+
+int sttsm_profile_read(int max, int* kind, int* level, double* flops, float* ms, int* count)
+{
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    if (count) *count = (int)g_prof.size();
+    for (int i = 0; i < (int)g_prof.size() && i < max; ++i) {
+        ProfRec& r = g_prof[i];
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return STTSM_ERR_CUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return STTSM_ERR_CUDA;
+        if (kind) kind[i] = r.kind;
+        if (level) level[i] = r.level;
+        if (flops) flops[i] = r.flops;
+        if (ms) ms[i] = t;
+    }
+    return STTSM_OK;
+}
+
 int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_t* tiles, int64_t tiles_cap,
                      int32_t* G, int64_t G_cap, int64_t* ntiles_out, int64_t* nG_out, int64_t* info)
 {
@@ -259,7 +323,10 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
     TcInst ti;
     memset(&ti, 0, sizeof(ti));
     if (!fp64) {
-        rc = cuda_err(launch_split_x((const float*)X, ws + w.xpieces, (int)p, (int)n, w.rows, w.Kp, np, stream));
+        {
+            ProfScope ps(stream, 2, -1, 0.0);
+            rc = cuda_err(launch_split_x((const float*)X, ws + w.xpieces, (int)p, (int)n, w.rows, w.Kp, np, stream));
+        }
         if (rc != STTSM_OK) return rc;
         rc = make_x_tensor_map(&ti.tmX, ws + w.xpieces, np, w.rows, w.Kp);
         if (rc != STTSM_OK) return rc;
@@ -281,6 +348,8 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
         L.rows_per_parent = LS.P_out * s.R;
         int64_t bp = 1;
         for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
+        const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
+        ProfScope ps(stream, fp64 ? 0 : 1, d, lflops);
         if (fp64) rc = cuda_err(launch_level_fp64(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
         else rc = cuda_err(launch_level_tc(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
         if (rc != STTSM_OK) return rc;

@@ -14,15 +14,29 @@
 // (x = x_0 + x_1 + x_2 + rounding); the products x_s * y_t with s + t <= NP-1
 // are accumulated in FP32 in tensor memory (6 products for NP = 3, 3 for NP = 2).
 //
-// CTA = 9 warps, one CTA per SM, persistent over the tile list:
-//   warps 0-3  epilogue: tcgen05.ld of the 128 x N FP32 tile, scatter to HBM;
-//   warps 4-7  producers: thread t gathers row t of the A tile (32 contraction
-//              indices per stage) with plain loads, splits it into BF16
-//              pieces and writes them in the SW64 K-major layout;
-//              thread 128 also issues the TMA load of the X pieces;
-//   warp 8     TMEM allocation and the single MMA-issuing thread.
-// Stages: A = NP x 128 x 32 BF16, B = NP x 256 x 32 BF16, mbarrier pipeline;
-// two TMEM accumulators (2 x 256 columns) overlap epilogue and MMA.
+// Accumulation: the tensor core's FP32 accumulation into a large running
+// sum loses low-order bits on every MMA, so the two kinds of products go to
+// separate tensor-memory accumulators:
+//   D0 (columns 256-511): x_0 * y_0 only, restarted every GS stages (64
+//       contraction indices); the epilogue warps add each partial into an
+//       FP32 register running sum (round-to-nearest);
+//   D1 (columns 0-255): every cross product (s + t >= 1), accumulated over
+//       the whole contraction; its values are ~2^-8 of D0's, so its rounding
+//       is ~2^-8 smaller.
+// The tile result is (sum of D0 partials) + D1.
+//
+// CTA = 17 warps, one CTA per SM, persistent over the tile list:
+//   warps 0-15  workers.  Warp w serves TMEM lanes / tile rows 32 (w % 4) ..
+//               +31 and chunk c = w / 4: per stage each thread gathers the 8
+//               contraction entries 8c .. 8c+7 of its row with plain loads,
+//               splits them into BF16 pieces and writes one 16-byte chunk per
+//               piece in the SW64 K-major layout; thread 0 also issues the
+//               TMA load of the X pieces.  As epilogue the warp owns the 64
+//               columns 64c .. 64c+63: after producing each group it folds
+//               the previous group's D0 partial into FP32 registers; at the
+//               end of a tile it adds D1 and scatters the row to HBM.
+//   warp 16     TMEM allocation and the single MMA-issuing thread.
+// Stages: A = NP x 128 x 32 BF16, B = NP x 256 x 32 BF16, mbarrier pipeline.
 // Every wait is bounded (2 s of globaltimer); on expiry the CTA records
 // status 1, stops, drains, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -34,7 +48,10 @@ namespace sttsm {
 
 namespace {
 
-constexpr int NUM_THREADS = 288;
+constexpr int NUM_THREADS = 544;
+constexpr int WORK_WARPS = 16;
+constexpr int MMA_WARP = 16;
+constexpr int GS = 2;   // stages per D0 flush group (64 contraction indices)
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -124,22 +141,17 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t
         :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum) : "memory");
 }
 
-// 32 lanes x 32 consecutive FP32 columns; thread i receives lane (base + i).
-__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float* v)
+// 32 lanes x 8 consecutive FP32 columns; thread i receives lane (base + i).
+__device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, float* v)
 {
-    uint32_t r[32];
+    uint32_t r[8];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading and
@@ -186,30 +198,34 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
 {
     using S = Smem<NP>;
     constexpr int STAGES = S::STAGES;
+    static_assert(STAGES > GS, "producers must be able to run a whole group ahead of the flush");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = (uint64_t*)(smem + STAGES * S::STAGE);
-    // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain
-    uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
+    // bars: full[STAGES], empty[STAGES], d0_full, d0_empty, d1_empty, drain
+    uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 4);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
-    auto accf_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
-    auto acce_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
-    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+    const uint32_t d0_full = bar0 + 8u * (2 * STAGES);
+    const uint32_t d0_empty = bar0 + 8u * (2 * STAGES + 1);
+    const uint32_t d1_empty = bar0 + 8u * (2 * STAGES + 2);
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 3);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 129); mbar_init(empty_bar(s), 1); }
-        for (int a = 0; a < 2; ++a) { mbar_init(accf_bar(a), 1); mbar_init(acce_bar(a), 128); }
+        for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), WORK_WARPS * 32 + 1); mbar_init(empty_bar(s), 1); }
+        mbar_init(d0_full, 1);
+        mbar_init(d0_empty, WORK_WARPS);
+        mbar_init(d1_empty, WORK_WARPS);
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
-    if (warp == 8) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(smem_u32(tmem_holder)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
@@ -217,28 +233,59 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
+    const uint32_t tmem_d1 = tmem_base;
+    const uint32_t tmem_d0 = tmem_base + (uint32_t)TC_BN;
 
-    if (warp >= 4 && warp < 8) {
-        // ------------------------------------------------------------ producers
-        const int pt = threadIdx.x - 128;                // row of the A tile
-        const bool tma_thread = (pt == 0);
+    if (warp < WORK_WARPS) {
+        // ------------------------------------------------------------ workers
+        const int quad = warp & 3, cq = warp >> 2;
+        const int row = quad * 32 + lane;                 // tile row and TMEM lane
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        const int colbase = cq * 64;                      // epilogue columns
+        const bool tma_thread = threadIdx.x == 0;
         int stage = 0;
         uint32_t phase = 0;
+        uint32_t group_phase = 0;
         int last_stage_issued = -1;
         uint32_t last_phase_issued = 0;
         bool ok = true;
+        float acc[64];
+
+        // fold the D0 partial of one group into acc (all 16 warps, warp-uniform)
+        auto flush = [&](bool active) -> bool {
+            if (!mbar_wait(d0_full, group_phase, abort_flag, status)) return false;
+            group_phase ^= 1u;
+            tc_fence_after();
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float v[8];
+                    tmem_ld_32x32b_x8(tmem_d0 + lane_off + colbase + c * 8, v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(d0_empty);
+            return true;
+        };
+
         for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
             const Tile t = tiles[ti];
             const TcInst& TI = insts ? insts[t.inst] : inst0;
             const LevelInst& I = TI.L;
             const float* pbase = (const float*)I.parent + (int64_t)t.parent * I.P_parent * I.bm;
-            const int64_t g = (int64_t)t.row0 + pt;
+            const int64_t g = (int64_t)t.row0 + row;
             const bool valid = g < I.rows_per_parent;
             const int pr = valid ? (int)(g / I.R) : 0;
             const int rr = valid ? (int)(g % I.R) : 0;
             const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
             const int b = I.b, nbar = I.nbar;
             const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
+            const bool active = colbase < t.ncols;        // warp-uniform
+#pragma unroll
+            for (int i = 0; i < 64; ++i) acc[i] = 0.f;
             for (int ks = 0; ks < nk; ++ks) {
                 if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                 uint8_t* sA = smem + stage * S::STAGE;
@@ -250,9 +297,10 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
                     last_stage_issued = stage;
                     last_phase_issued = phase;
                 }
-                // gather 32 contraction entries of this row
-                float v[TC_KC];
-                int ib = k0 / b, a = k0 - ib * b;
+                // gather the 8 contraction entries k0 + 8 cq .. +7 of this row
+                float v[8];
+                const int kk0 = k0 + cq * 8;
+                int ib = kk0 / b, a = kk0 - ib * b;
                 const float* src = pbase;
                 int64_t stride = 0;
                 bool live = false;
@@ -269,39 +317,65 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
                 };
                 seg();
 #pragma unroll
-                for (int e = 0; e < TC_KC; ++e) {
+                for (int e = 0; e < 8; ++e) {
                     v[e] = live ? __ldg(src) : 0.f;
                     if (live) src += stride;
                     if (++a == b) { a = 0; ++ib; seg(); }
                 }
-                // split into BF16 pieces and store the row (SW64 K-major: row r
-                // at r*64 B, 16-byte chunk c at (c ^ ((r >> 1) & 3)) * 16)
-                const uint32_t rowbase = smem_u32(sA) + pt * 64;
-                const int sw = (pt >> 1) & 3;
+                // split into BF16 pieces; piece pc goes to plane pc, row `row`,
+                // 16-byte chunk cq (SW64 K-major: chunk at (cq ^ ((row >> 1) & 3)) * 16)
+                const uint32_t addr0 = smem_u32(sA) + row * 64 + ((cq ^ ((row >> 1) & 3)) << 4);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t w[NP][4];
+                for (int pc = 0; pc < NP; ++pc) {
+                    uint32_t w[4];
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
-                        float x0 = v[c * 8 + 2 * h], x1 = v[c * 8 + 2 * h + 1];
-#pragma unroll
-                        for (int pc = 0; pc < NP; ++pc) {
-                            __nv_bfloat16 b0 = __float2bfloat16_rn(x0), b1 = __float2bfloat16_rn(x1);
-                            w[pc][h] = pack_bf16x2(b0, b1);
-                            x0 -= __bfloat162float(b0);
-                            x1 -= __bfloat162float(b1);
-                        }
+                        const __nv_bfloat16 b0 = __float2bfloat16_rn(v[2 * h]), b1 = __float2bfloat16_rn(v[2 * h + 1]);
+                        w[h] = pack_bf16x2(b0, b1);
+                        v[2 * h] -= __bfloat162float(b0);
+                        v[2 * h + 1] -= __bfloat162float(b1);
                     }
-#pragma unroll
-                    for (int pc = 0; pc < NP; ++pc) {
-                        const uint32_t addr = rowbase + pc * S::A_PLANE + ((c ^ sw) << 4);
-                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                                     :: "r"(addr), "r"(w[pc][0]), "r"(w[pc][1]), "r"(w[pc][2]), "r"(w[pc][3]) : "memory");
-                    }
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                                 :: "r"(addr0 + pc * S::A_PLANE), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
                 }
                 fence_proxy_async();
                 mbar_arrive(full_bar(stage));
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                // a group is fully produced: fold the previous group's D0 partial
+                if (((ks % GS) == GS - 1 || ks == nk - 1) && ks >= GS) {
+                    if (!flush(active)) { ok = false; break; }
+                }
+            }
+            if (!ok) break;
+            // the last group of the tile
+            if (!flush(active)) { ok = false; break; }
+            // every MMA of the tile has completed (last d0_full commit): add D1
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float v[8];
+                    tmem_ld_32x32b_x8(tmem_d1 + lane_off + colbase + c * 8, v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(d1_empty);
+            // scatter the row's 64 columns into the children's blocks
+            if (active && valid) {
+                const int bk = I.bpow[I.k];
+                float* out = (float*)I.out;
+                const int64_t rowoff = (rr % bk) + (int64_t)bk * b * (rr / bk);
+                const int cg0 = t.col0 + colbase;
+                int jb = cg0 / b, c = cg0 - jb * b;
+                float* dst = out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
+                const int nvalid = t.ncols - colbase;
+#pragma unroll
+                for (int e = 0; e < 64; ++e) {
+                    if (e < nvalid) dst[(int64_t)bk * c] = acc[e];
+                    if (++c == b) { c = 0; ++jb; dst += I.P_out * I.bm; }
+                }
             }
         }
         // make sure no TMA write is still in flight before the CTA exits
@@ -310,13 +384,13 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
             while (!mbar_try_wait(full_bar(last_stage_issued), last_phase_issued))
                 if (globaltimer() - t0 > WAIT_LIMIT_NS) break;
         }
-    } else if (warp == 8) {
+    } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t acc_phase = 0;   // bit a = phase of accumulator a
-            int acc = 0;
+            uint32_t group_phase = 0;   // d0_empty parity counter
+            uint32_t tile_phase = 0;    // d1_empty parity counter
             bool ok = true;
             bool issued = false;
             for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
@@ -325,36 +399,48 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
                 const int nk = (TI.L.Ktot + TC_KC - 1) / TC_KC;
                 const int nmma = (t.ncols + 15) & ~15;
                 const uint32_t idesc = idesc_bf16(nmma);
-                if (!mbar_wait(acce_bar(acc), ((acc_phase >> acc) & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+                // the workers have read D1 of the previous tile
+                if (!mbar_wait(d1_empty, tile_phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                tile_phase ^= 1u;
                 tc_fence_after();
-                const uint32_t tmem_d = tmem_base + (uint32_t)(acc * TC_BN);
                 for (int ks = 0; ks < nk; ++ks) {
                     if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sA = smem_u32(smem + stage * S::STAGE);
                     const uint32_t sB = sA + NP * S::A_PLANE;
+                    // cross products (s + u >= 1) into D1
 #pragma unroll
                     for (int kh = 0; kh < TC_KC / 16; ++kh) {
 #pragma unroll
                         for (int s = 0; s < NP; ++s) {
 #pragma unroll
                             for (int u = 0; u < NP; ++u) {
-                                if (s + u > NP - 1) continue;
+                                if (s + u > NP - 1 || s + u == 0) continue;
                                 const uint64_t ad = smem_desc_sw64(sA + s * S::A_PLANE + kh * 32);
                                 const uint64_t bd = smem_desc_sw64(sB + u * S::B_PLANE + kh * 32);
-                                const uint32_t accum = (ks > 0 || kh > 0 || s > 0 || u > 0) ? 1u : 0u;
-                                tc_mma(tmem_d, ad, bd, idesc, accum);
+                                const bool first = ks == 0 && kh == 0 && s == 0 && u == 1;
+                                tc_mma(tmem_d1, ad, bd, idesc, first ? 0u : 1u);
                                 issued = true;
                             }
                         }
                     }
+                    // hi x hi into D0, restarted at each group
+                    const bool group_start = (ks % GS) == 0;
+                    if (group_start) {
+                        if (!mbar_wait(d0_empty, group_phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                        group_phase ^= 1u;
+                        tc_fence_after();
+                    }
+#pragma unroll
+                    for (int kh = 0; kh < TC_KC / 16; ++kh) {
+                        const uint64_t ad = smem_desc_sw64(sA + kh * 32);
+                        const uint64_t bd = smem_desc_sw64(sB + kh * 32);
+                        tc_mma(tmem_d0, ad, bd, idesc, (group_start && kh == 0) ? 0u : 1u);
+                    }
                     tc_commit(empty_bar(stage));
+                    if ((ks % GS) == GS - 1 || ks == nk - 1) tc_commit(d0_full);
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
-                if (!ok) break;
-                tc_commit(accf_bar(acc));
-                acc_phase ^= 1u << acc;
-                acc ^= 1;
             }
             if (!ok && issued) {
                 // drain: wait for every MMA issued so far before TMEM is freed
@@ -365,51 +451,12 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
             }
         }
         __syncwarp();
-    } else {
-        // ------------------------------------------------------------ epilogue (warps 0-3)
-        const int row = warp * 32 + lane;
-        uint32_t acc_phase = 0;   // bit a = phase of accumulator a
-        int acc = 0;
-        for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-            const Tile t = tiles[ti];
-            const TcInst& TI = insts ? insts[t.inst] : inst0;
-            const LevelInst& I = TI.L;
-            if (!mbar_wait(accf_bar(acc), (acc_phase >> acc) & 1u, abort_flag, status)) break;
-            tc_fence_after();
-            const int64_t g = (int64_t)t.row0 + row;
-            const bool valid = g < I.rows_per_parent;
-            const int pr = valid ? (int)(g / I.R) : 0;
-            const int rr = valid ? (int)(g % I.R) : 0;
-            const int bk = I.bpow[I.k];
-            const int b = I.b;
-            float* out = (float*)I.out;
-            const int64_t rowoff = (rr % bk) + (int64_t)bk * b * (rr / bk);
-            const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * TC_BN);
-            for (int c0 = 0; c0 < t.ncols; c0 += 32) {
-                float v[32];
-                tmem_ld_32x32b_x32(taddr + c0, v);
-                if (valid) {
-                    int cg = t.col0 + c0;
-                    int jb = cg / b, c = cg - jb * b;
-                    float* dst = out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        if (c0 + e < t.ncols) dst[(int64_t)bk * c] = v[e];
-                        if (++c == b) { c = 0; ++jb; dst += I.P_out * I.bm; }
-                    }
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(acce_bar(acc));
-            acc_phase ^= 1u << acc;
-            acc ^= 1;
-        }
     }
 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem_base));
     }
 }
