@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the headline step only (no e2e, FP64 path, check or CPU baseline); for profiling")
     return ap.parse_args()
 
 
@@ -248,6 +250,69 @@ def time_steps(torch, fn, steps, warmup, per_step_events=True):
     return t_all0.elapsed_time(t_all1), per
 
 
+def end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, steps):
+    """Same metric through sttsm_bcss_host: H2D of A and X from pinned host
+    buffers, the computation, D2H of C, all inside the timed region."""
+    hA = A.cpu().pin_memory()
+    hX = torch.from_numpy(xcol32(Xh)).pin_memory()
+    hC = torch.empty(C.numel(), dtype=torch.float32).pin_memory()
+    dA2, dX2, dC2 = torch.empty_like(A), torch.empty(hX.numel(), dtype=torch.float32, device="cuda"), torch.empty_like(C)
+
+    def e2e_step():
+        st.sttsm_bcss_host(hA, hX, M, N, P, b, hC, prec, dA2, dX2, dC2, ws)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+    assert np.array_equal(hC.numpy(), C.cpu().numpy())
+    return {"value": F / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+            "h2d_bytes_per_step": int(hA.numel() * 4 + hX.numel() * 4), "d2h_bytes_per_step": int(hC.numel() * 4),
+            "timer": "host wall clock around sttsm_bcss_host + stream sync", "steps": steps}
+
+
+def fp64_path(st, torch, Xh, b, F, ms):
+    """The plain FP64 GPU path (CUDA-core FMAs) on the same workload."""
+    A64 = make_device_inputs(st, torch, b, torch.float64)
+    dX64 = torch.from_numpy(np.asfortranarray(Xh).reshape(-1, order="F").copy()).cuda()
+    C64 = torch.empty(st.bcss_num_elems(M, P, b), dtype=torch.float64, device="cuda")
+    ws64 = st.workspace_tensor(M, N, P, b, st.STTSM_FP64)
+    tot64, _ = time_steps(torch, lambda: st.sttsm_bcss(A64, dX64, M, N, P, b, C64, st.STTSM_FP64, ws64), 2, 1)
+    ms64 = tot64 / 2
+    return ({"value": F / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
+             "speedup_of_split_path": ms64 / ms}, C64)
+
+
+def check_and_baseline(args, C, C64, Xh, X32, b, F, world):
+    """Sampled relative error of both paths against the FP64 oracle, and the
+    oracle itself timed on this host's cores (N = 1 only)."""
+    import oracle
+    import synth
+    oracle.build()
+    A_dense = synth.sym_uniform_dense(M, N, SEED_A)
+    J = np.sort(np.random.default_rng(SEED_J).integers(0, P, size=(256, M)), axis=1)
+    ref32 = oracle.sttsm_entries(A_dense, X32, M, J)
+    c32 = C.double().cpu().numpy()
+    got32 = np.array([c32[bcss_pos(j, b)] for j in J])
+    rel_err = {"samples": 256, args.prec: float(np.linalg.norm(got32 - ref32) / np.linalg.norm(ref32)),
+               "tolerance": {args.prec: 1e-6, "fp64": 1e-12}}
+    if C64 is not None:
+        ref64 = oracle.sttsm_entries(A_dense, Xh, M, J)
+        c64 = C64.cpu().numpy()
+        got64 = np.array([c64[bcss_pos(j, b)] for j in J])
+        rel_err["fp64"] = float(np.linalg.norm(got64 - ref64) / np.linalg.norm(ref64))
+    cpu_base = None
+    if world == 1:
+        dt, S = oracle_slice_rate(A_dense, X32, args.cpu_seconds)
+        cpu_base = {"value": F * S / P / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_threads(), "kind": "oracle",
+                    "sample": "FP64 oracle dense mode-product chain (A x_2 X_S x_1 X x_0 X) for %d of %d "
+                              "slices C[:,:,j], %.1f s; value = BCSS flop count x %d/%d / time" % (S, P, dt, S, P)}
+    return rel_err, cpu_base
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -345,64 +410,17 @@ def main():
                 "kernel_share_of_step": kern_ms / total_ms if total_ms > 0 else None,
                 "levels": levels}
 
-    # ---- end to end through the host-buffer entry point
-    hA = A.cpu().pin_memory()
-    hX = torch.from_numpy(xcol32(Xh)).pin_memory()
-    hC = torch.empty(C.numel(), dtype=torch.float32).pin_memory()
-    dA2, dX2, dC2 = torch.empty_like(A), torch.empty_like(dX), torch.empty_like(C)
-
-    def e2e_step():
-        st.sttsm_bcss_host(hA, hX, M, N, P, b, hC, prec, dA2, dX2, dC2, ws)
-        torch.cuda.current_stream().synchronize()
-
-    e2e_steps = max(3, args.steps // 2)
-    for _ in range(2):
-        e2e_step()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    e2e = {"value": F / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-           "h2d_bytes_per_step": int(hA.numel() * 4 + hX.numel() * 4), "d2h_bytes_per_step": int(hC.numel() * 4),
-           "timer": "host wall clock around sttsm_bcss_host + stream sync"}
-    assert np.array_equal(hC.numpy(), C.cpu().numpy())
-    del hA, dA2, dC2
-
-    # ---- plain FP64 GPU path on the same workload
-    fp64 = None
-    if rank == 0:
-        A64 = make_device_inputs(st, torch, b, torch.float64)
-        dX64 = torch.from_numpy(np.asfortranarray(Xh).reshape(-1, order="F").copy()).cuda()
-        C64 = torch.empty(st.bcss_num_elems(M, P, b), dtype=torch.float64, device="cuda")
-        ws64 = st.workspace_tensor(M, N, P, b, st.STTSM_FP64)
-        tot64, _ = time_steps(torch, lambda: st.sttsm_bcss(A64, dX64, M, N, P, b, C64, st.STTSM_FP64, ws64), 2, 1)
-        ms64 = tot64 / 2
-        fp64 = {"value": F / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
-                "speedup_of_split_path": (F / (ms * 1e-3) / 1e12) / (F / (ms64 * 1e-3) / 1e12)}
-
-    # ---- accuracy against the oracle and the CPU baseline (rank 0, N = 1)
-    rel_err = None
-    cpu_base = None
-    if rank == 0 and not args.no_check:
-        import oracle
-        oracle.build()
-        A_dense = synth.sym_uniform_dense(M, N, SEED_A)
-        J = np.sort(np.random.default_rng(SEED_J).integers(0, P, size=(256, M)), axis=1)
-        ref32 = oracle.sttsm_entries(A_dense, X32, M, J)
-        ref64 = oracle.sttsm_entries(A_dense, Xh, M, J)
-        c32 = C.double().cpu().numpy()
-        got32 = np.array([c32[bcss_pos(j, b)] for j in J])
-        rel_err = {"samples": 256, args.prec: float(np.linalg.norm(got32 - ref32) / np.linalg.norm(ref32)),
-                   "tolerance": {args.prec: 1e-6, "fp64": 1e-12}}
-        if fp64 is not None:
-            c64 = C64.cpu().numpy()
-            got64 = np.array([c64[bcss_pos(j, b)] for j in J])
-            rel_err["fp64"] = float(np.linalg.norm(got64 - ref64) / np.linalg.norm(ref64))
-        if world == 1:
-            dt, S = oracle_slice_rate(A_dense, X32, args.cpu_seconds)
-            cpu_base = {"value": F * S / P / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_threads(), "kind": "oracle",
-                        "sample": "FP64 oracle dense mode-product chain (A x_2 X_S x_1 X x_0 X) for %d of %d "
-                                  "slices C[:,:,j], %.1f s; value = BCSS flop count x %d/%d / time" % (S, P, dt, S, P)}
+    e2e = fp64 = rel_err = cpu_base = None
+    C64 = None
+    if not args.no_extras:
+        # ---- end to end through the host-buffer entry point
+        e2e = end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, max(3, args.steps // 10))
+        # ---- plain FP64 GPU path on the same workload (rank 0)
+        if rank == 0:
+            fp64, C64 = fp64_path(st, torch, Xh, b, F, ms)
+        # ---- accuracy against the oracle and the CPU baseline (rank 0; baseline at N = 1)
+        if rank == 0 and not args.no_check:
+            rel_err, cpu_base = check_and_baseline(args, C, C64, Xh, X32, b, F, world)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
