@@ -138,6 +138,31 @@ int sttsm_bcss_host(const void* A_bcss, const void* X, int m, int64_t n, int64_t
                     void* C_bcss, int prec, void* dA, void* dX, void* dC,
                     void* workspace, size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of sttsm_bcss.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * where they call it — code under a fixed, pre-reserved memory budget
+ * (embedded and real-time services), plug-ins hosted by a framework that
+ * owns every device allocation, and paths where an allocation could stall
+ * or fail at an unpredictable moment.  It takes only the inputs and the
+ * output; it calls no cudaMalloc, cudaFree or other allocating routine.
+ *   Workspace: one file-scope device array of STTSM_NOALLOC_SCRATCH_BYTES
+ *   (64 MiB) that every GPU loading the library holds until the process
+ *   exits.  It carries the split X pieces, the temporaries and the level
+ *   plans.  Shapes that need more return STTSM_ERR_NOMEM before any launch
+ *   (m = 3, n = p = 128, b = 32 fits; use sttsm_bcss with a caller
+ *   workspace beyond that).
+ *   Set-up: the first call on each device looks up the array's device
+ *   address (cudaGetSymbolAddress) and zeroes its status word; make that
+ *   first call before any stream capture.
+ *   Sharing: every call uses the same array and finds the previous call's
+ *   contents there.  Calls that overlap on the GPU (several streams or host
+ *   threads) race on it and corrupt each other: serialise them.  Device-side
+ *   wait timeouts are recorded in the array, not in sttsm_device_status.
+ * Arguments, layouts and results are those of sttsm_bcss. */
+#define STTSM_NOALLOC_SCRATCH_BYTES (64u << 20)
+int sttsm_bcss_noalloc(const void* A_bcss, const void* X, int m, int64_t n, int64_t p, int b,
+                       void* C_bcss, int prec, void* stream);
+
 /* Device status word: 0 = fine; otherwise the code of the last device-side
  * failure (1 = bounded wait timed out).  Reading clears it. */
 int sttsm_device_status(void);

@@ -81,6 +81,8 @@ def _load():
     L.sttsm_bcss_host.restype = i32
     L.sttsm_device_status.argtypes = []
     L.sttsm_device_status.restype = i32
+    L.sttsm_bcss_noalloc.argtypes = [P, P, i32, i64, i64, i32, P, i32, P]
+    L.sttsm_bcss_noalloc.restype = i32
     L.sttsm_profile_enable.argtypes = [i32]
     L.sttsm_profile_enable.restype = i32
     L.sttsm_profile_read.argtypes = [i32, P, P, P, P, P]
@@ -95,7 +97,8 @@ def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points this binding loads."""
     return ["bcss_num_blocks", "bcss_num_elems", "bcss_block_rank", "bcss_block_unrank", "sttsm_flops",
             "bcss_pack", "bcss_unpack", "sttsm_workspace_size", "sttsm_bcss", "sttsm_bcss_host",
-            "sttsm_device_status", "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read"]
+            "sttsm_device_status", "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read",
+            "sttsm_bcss_noalloc"]
 
 
 def _check(fn: str, rc: int) -> None:
@@ -205,6 +208,17 @@ def sttsm_bcss(A, X, m: int, n: int, p: int, b: int, C, prec: int, workspace, st
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("sttsm_bcss", _load().sttsm_bcss(_dptr(A), _dptr(X), m, n, p, b, _dptr(C), prec, ws, nbytes,
                                             _stream(stream)))
+
+
+def sttsm_bcss_noalloc(A, X, m: int, n: int, p: int, b: int, C, prec: int, stream=None) -> None:
+    """sttsm_bcss without a caller workspace and without allocating: for callers
+    that may not allocate device memory at the call site (fixed memory budgets,
+    framework-owned allocators).  Uses the library's fixed 64 MiB device scratch
+    array; calls that overlap on the GPU race on it.  The first call on a device
+    sets the array up and should come before any stream capture."""
+    _check_operands(A, X, C, m, n, p, b, prec)
+    _check("sttsm_bcss_noalloc", _load().sttsm_bcss_noalloc(_dptr(A), _dptr(X), m, n, p, b, _dptr(C), prec,
+                                                            _stream(stream)))
 
 
 def sttsm_bcss_host(A, X, m: int, n: int, p: int, b: int, C, prec: int, dA, dX, dC, workspace, stream=None) -> None:
