@@ -191,6 +191,77 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
 
 }  // namespace
 
+// Row state of one worker thread for one tile: where its gathered A-operand
+// row comes from (see common.cuh for the index maps).
+struct GatherRow {
+    const float* pbase;      // parent node base
+    const int32_t* Grow;     // G row of the thread's output prefix block
+    int rr;                  // row inside the output block
+    bool valid;
+};
+
+// The 8 contraction entries kk0 .. kk0+7 of a row.  Within one stored block
+// the entries of a row are b^q apart; with q = 0 they are contiguous and are
+// read with two 16-byte loads when aligned.
+__device__ __forceinline__ void gather8(const GatherRow& R, const LevelInst& I, int kk0, float* v)
+{
+    const int b = I.b;
+    int ib = kk0 / b, a = kk0 - ib * b;
+    if (!R.valid) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        return;
+    }
+    if (a + 8 <= b && ib < I.nbar) {
+        const int32_t gq = __ldg(R.Grow + ib);
+        const int q = gq & 7;
+        const int bq = I.bpow[q];
+        const float* src = R.pbase + (int64_t)(gq >> 3) * I.bm + (R.rr % bq) + (int64_t)bq * b * (R.rr / bq) + (int64_t)a * bq;
+        if (q == 0 && ((uintptr_t)src & 15) == 0) {
+            const float4 x0 = __ldg((const float4*)src), x1 = __ldg((const float4*)src + 1);
+            v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+            v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = __ldg(src + (int64_t)e * bq);
+        }
+        return;
+    }
+    // general case: the 8 entries cross block boundaries (b < 8 or unaligned)
+    const float* src = R.pbase;
+    int64_t stride = 0;
+    bool live = false;
+    auto seg = [&]() {
+        live = ib < I.nbar;
+        if (live) {
+            const int32_t gq = __ldg(R.Grow + ib);
+            const int q = gq & 7;
+            const int bq = I.bpow[q];
+            stride = bq;
+            src = R.pbase + (int64_t)(gq >> 3) * I.bm + (R.rr % bq) + (int64_t)bq * b * (R.rr / bq) + (int64_t)a * bq;
+        }
+    };
+    seg();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        v[e] = live ? __ldg(src) : 0.f;
+        if (live) src += stride;
+        if (++a == b) { a = 0; ++ib; seg(); }
+    }
+}
+
+__device__ __forceinline__ GatherRow gather_row(const Tile& t, const LevelInst& I, int row)
+{
+    GatherRow R;
+    const int64_t g = (int64_t)t.row0 + row;
+    R.valid = g < I.rows_per_parent;
+    const int pr = R.valid ? (int)(g / I.R) : 0;
+    R.rr = R.valid ? (int)(g % I.R) : 0;
+    R.pbase = (const float*)I.parent + (int64_t)t.parent * I.P_parent * I.bm;
+    R.Grow = I.G + (int64_t)pr * I.nbar;
+    return R;
+}
+
 template <int NP>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__ insts,
@@ -250,6 +321,8 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
         uint32_t last_phase_issued = 0;
         bool ok = true;
         float acc[64];
+        float vn[8];
+        bool prefetched = false;
 
         // fold the D0 partial of one group into acc (all 16 warps, warp-uniform)
         auto flush = [&](bool active) -> bool {
@@ -275,17 +348,14 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
             const Tile t = tiles[ti];
             const TcInst& TI = insts ? insts[t.inst] : inst0;
             const LevelInst& I = TI.L;
-            const float* pbase = (const float*)I.parent + (int64_t)t.parent * I.P_parent * I.bm;
-            const int64_t g = (int64_t)t.row0 + row;
-            const bool valid = g < I.rows_per_parent;
-            const int pr = valid ? (int)(g / I.R) : 0;
-            const int rr = valid ? (int)(g % I.R) : 0;
-            const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
-            const int b = I.b, nbar = I.nbar;
+            const GatherRow GR = gather_row(t, I, row);
+            const bool valid = GR.valid;
             const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
             const bool active = colbase < t.ncols;        // warp-uniform
 #pragma unroll
             for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+            if (!prefetched) gather8(GR, I, cq * 8, vn);  // stage 0 of the tile
+            prefetched = false;
             for (int ks = 0; ks < nk; ++ks) {
                 if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                 uint8_t* sA = smem + stage * S::STAGE;
@@ -297,31 +367,6 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
                     last_stage_issued = stage;
                     last_phase_issued = phase;
                 }
-                // gather the 8 contraction entries k0 + 8 cq .. +7 of this row
-                float v[8];
-                const int kk0 = k0 + cq * 8;
-                int ib = kk0 / b, a = kk0 - ib * b;
-                const float* src = pbase;
-                int64_t stride = 0;
-                bool live = false;
-                auto seg = [&]() {
-                    live = valid && ib < nbar;
-                    if (live) {
-                        const int32_t gq = __ldg(Grow + ib);
-                        const int q = gq & 7;
-                        const int64_t rank = gq >> 3;
-                        const int bq = I.bpow[q];
-                        stride = bq;
-                        src = pbase + rank * I.bm + (rr % bq) + (int64_t)bq * b * (rr / bq) + (int64_t)a * bq;
-                    }
-                };
-                seg();
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    v[e] = live ? __ldg(src) : 0.f;
-                    if (live) src += stride;
-                    if (++a == b) { a = 0; ++ib; seg(); }
-                }
                 // split into BF16 pieces; piece pc goes to plane pc, row `row`,
                 // 16-byte chunk cq (SW64 K-major: chunk at (cq ^ ((row >> 1) & 3)) * 16)
                 const uint32_t addr0 = smem_u32(sA) + row * 64 + ((cq ^ ((row >> 1) & 3)) << 4);
@@ -330,10 +375,10 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
                     uint32_t w[4];
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
-                        const __nv_bfloat16 b0 = __float2bfloat16_rn(v[2 * h]), b1 = __float2bfloat16_rn(v[2 * h + 1]);
+                        const __nv_bfloat16 b0 = __float2bfloat16_rn(vn[2 * h]), b1 = __float2bfloat16_rn(vn[2 * h + 1]);
                         w[h] = pack_bf16x2(b0, b1);
-                        v[2 * h] -= __bfloat162float(b0);
-                        v[2 * h + 1] -= __bfloat162float(b1);
+                        vn[2 * h] -= __bfloat162float(b0);
+                        vn[2 * h + 1] -= __bfloat162float(b1);
                     }
                     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
                                  :: "r"(addr0 + pc * S::A_PLANE), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
@@ -341,6 +386,15 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
                 fence_proxy_async();
                 mbar_arrive(full_bar(stage));
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                // issue the next stage's gather; it stays in flight over the flush and the next wait
+                if (ks + 1 < nk) {
+                    gather8(GR, I, (ks + 1) * TC_KC + cq * 8, vn);
+                } else if (ti + (int)gridDim.x < ntiles) {
+                    const Tile tn = tiles[ti + gridDim.x];
+                    const LevelInst& In = (insts ? insts[tn.inst] : inst0).L;
+                    gather8(gather_row(tn, In, row), In, cq * 8, vn);
+                    prefetched = true;
+                }
                 // a group is fully produced: fold the previous group's D0 partial
                 if (((ks % GS) == GS - 1 || ks == nk - 1) && ks >= GS) {
                     if (!flush(active)) { ok = false; break; }
@@ -364,6 +418,9 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
             if (lane == 0) mbar_arrive(d1_empty);
             // scatter the row's 64 columns into the children's blocks
             if (active && valid) {
+                const int64_t g = (int64_t)t.row0 + row;
+                const int pr = (int)(g / I.R), rr = (int)(g % I.R);
+                const int b = I.b;
                 const int bk = I.bpow[I.k];
                 float* out = (float*)I.out;
                 const int64_t rowoff = (rr % bk) + (int64_t)bk * b * (rr / bk);
