@@ -52,6 +52,10 @@ def parse_args():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+                    help="single: m=3 n=p=768 instance (default); batch: 4096 mixed instances; serve: Poisson stream")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--ws-gb", type=float, default=48.0, help="batch workspace budget (GiB)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the headline step only (no e2e, FP64 path, check or CPU baseline); for profiling")
     return ap.parse_args()
@@ -313,10 +317,111 @@ def check_and_baseline(args, C, C64, Xh, X32, b, F, world):
     return rel_err, cpu_base
 
 
+def run_batch(args):
+    """Batched workload: count instances, m in {3,4,5} (weights .5/.3/.2), n in U{8..64},
+    p in U{8..n}, b per instance by sttsm_autotune_b over {4, 8, 16}; BF16X6; one
+    sttsm_batch_run (a CUDA-graph replay) per step.  Compared with a per-instance loop
+    of the plain FP64 path (sttsm_bcss per instance)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_7744_gb300 as st
+    import synth
+    prec = st.STTSM_BF16X6
+    shapes = synth.batch_shapes(3, args.batch_count)
+    maxdense = max(n ** m for m, n, _ in shapes)
+    scratch32 = torch.empty(maxdense, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    insts, xs = [], []
+    bcount = {}
+    for i, (m, n, p) in enumerate(shapes):
+        b = st.sttsm_autotune_b(m, n, p, prec, (4, 8, 16))
+        bcount[b] = bcount.get(b, 0) + 1
+        d = scratch32[: n ** m]
+        synth.dev_sym_uniform_dense(d.data_ptr(), m, n, 1000 + i, "f32", stream)
+        A = torch.empty(st.bcss_num_elems(m, n, b), dtype=torch.float32, device="cuda")
+        st.bcss_pack(d, A, m, n, b)
+        X = synth.x_gaussian(5000 + i, p, n)
+        xs.append(X)
+        dX = torch.from_numpy(xcol32(X)).cuda()
+        C = torch.empty(st.bcss_num_elems(m, p, b), dtype=torch.float32, device="cuda")
+        insts.append((A, dX, C, m, n, p, b))
+    torch.cuda.synchronize()
+    del scratch32
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    plan = st.BatchPlan(insts, prec, ws_budget=int(args.ws_gb * 2 ** 30))
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    ws = torch.empty(max(plan.workspace_size(), 1), dtype=torch.uint8, device="cuda")
+    F = info["useful_flops"]
+    t0 = time.perf_counter()
+    plan.run(ws)                       # captures the graph
+    torch.cuda.synchronize()
+    capture_s = time.perf_counter() - t0
+    steps = max(3, min(args.steps, 20))
+    clocks = ClockSampler()
+    clocks.start()
+    total_ms, per = time_steps(torch, lambda: plan.run(ws), steps, max(3, args.warmup))
+    clk = clocks.stop()
+    ms = total_ms / steps
+    value = F / (ms * 1e-3) / 1e12
+    # accuracy on a sample of instances against the oracle
+    import oracle
+    rng = np.random.default_rng(0)
+    errs = []
+    small = [i for i, (m, n, p) in enumerate(shapes) if n ** m <= 2e7]
+    for i in rng.choice(small, size=min(16, len(small)), replace=False):
+        A_, dX_, C_, m, n, p, b = insts[i]
+        X32 = xs[i].astype(np.float32).astype(np.float64)
+        Ad = synth.sym_uniform_dense(m, n, 1000 + int(i))
+        ref = oracle.bcss_pack(oracle.sttsm_chain(Ad, X32, m), m, p, b)
+        got = C_.double().cpu().numpy()
+        errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    # the per-instance loop of the plain FP64 path
+    scratch64 = torch.empty(maxdense, dtype=torch.float64, device="cuda")
+    f64 = []
+    for i, (A_, dX_, C_, m, n, p, b) in enumerate(insts):
+        d = scratch64[: n ** m]
+        synth.dev_sym_uniform_dense(d.data_ptr(), m, n, 1000 + i, "f64", stream)
+        A64 = torch.empty(st.bcss_num_elems(m, n, b), dtype=torch.float64, device="cuda")
+        st.bcss_pack(d, A64, m, n, b)
+        X64 = torch.from_numpy(np.asfortranarray(xs[i]).reshape(-1, order="F").copy()).cuda()
+        C64 = torch.empty(st.bcss_num_elems(m, p, b), dtype=torch.float64, device="cuda")
+        f64.append((A64, X64, C64, m, n, p, b, st.workspace_tensor(m, n, p, b, st.STTSM_FP64)))
+    del scratch64
+    torch.cuda.synchronize()
+
+    def loop64():
+        for (A64, X64, C64, m, n, p, b, w64) in f64:
+            st.sttsm_bcss(A64, X64, m, n, p, b, C64, st.STTSM_FP64, w64)
+
+    tot64, _ = time_steps(torch, loop64, 1, 1)
+    line = {"metric": "sttsm batch TFLOP/s (paper's BCSS flop count), BF16X6, one graph replay per step",
+            "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "p99_ms_per_step": float(np.percentile(per, 99)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x6", "data": "synthetic",
+            "config": {"workload": "batch of %d sttsm instances: m in {3,4,5} (.5/.3/.2), n U{8..64}, p U{8..n}, "
+                                   "b autotuned from {4,8,16}" % len(shapes),
+                       "b_counts": {str(k): v for k, v in sorted(bcount.items())}, "useful_flops_per_step": F,
+                       "waves": info["waves"], "workspace_gb": plan.workspace_size() / 2 ** 30,
+                       "plan_seconds": plan_s, "graph_capture_seconds": capture_s},
+            "fp64_per_instance_loop": {"value": F / (tot64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms": tot64,
+                                       "speedup_of_batch": tot64 / ms},
+            "rel_err": {"instances_checked": len(errs), "max": max(errs), "median": float(np.median(errs)),
+                        "tolerance": 1e-6},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    plan.destroy()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     import torch
     import torch.distributed as dist
 

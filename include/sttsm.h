@@ -138,6 +138,48 @@ int sttsm_bcss_host(const void* A_bcss, const void* X, int m, int64_t n, int64_t
                     void* C_bcss, int prec, void* dA, void* dX, void* dC,
                     void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------ batches (device) */
+
+/* One sttsm instance of a batch: device pointers to A (BCSS, block size b),
+ * X (p x n column-major) and C (BCSS), in the element type of the batch's
+ * precision. */
+typedef struct {
+    const void* A;
+    const void* X;
+    void* C;
+    int m;
+    int64_t n, p;
+    int b;
+} sttsm_desc;
+
+/* Block size for one instance: the candidate whose tile plan the cost model
+ * rates cheapest (split precisions: per-stage MMA time vs gather latency plus
+ * a per-tile overhead, summed over every tile of every level; FP64: the
+ * Tbl. 4 flop count).  Returns the chosen b (> 0) or an sttsm_status. */
+int sttsm_autotune_b(int m, int64_t n, int64_t p, int prec, const int* cands, int ncand);
+
+/* Batch plan: many independent instances (different m, n, p, b) run as one
+ * sequence of launches — per wave, one X-split launch and one launch per
+ * level d covering the level-d tiles of every instance with m > d (Fig. 5's
+ * levels, with each instance's own plan).  Instances are grouped into
+ * waves whose workspaces fit ws_budget bytes (0 = one wave).  The plan owns
+ * its tile lists and descriptor tables (device memory).  The descriptors'
+ * pointers are captured: the buffers must stay valid while the plan lives.
+ * STTSM_ERR_NOMEM if one instance alone exceeds the budget. */
+int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_budget, void** plan);
+int sttsm_batch_workspace_size(const void* plan, size_t* bytes);
+int sttsm_batch_info(const void* plan, int* waves, double* useful_flops);
+
+/* Runs the plan on `stream`.  The first run for a given workspace captures
+ * the whole launch sequence into a CUDA graph (on an internal stream); later
+ * runs replay it with one cudaGraphLaunch.  Every instance's C is written in
+ * full, bit-identical to sttsm_bcss on that instance alone. */
+int sttsm_batch_run(void* plan, void* workspace, size_t ws_bytes, void* stream);
+int sttsm_batch_plan_destroy(void* plan);
+
+/* One-shot batch: plan, run, synchronise `stream`, destroy. */
+int sttsm_batch(const sttsm_desc* d, int count, int prec, void* workspace, size_t ws_bytes, void* stream);
+
 /* Allocation-free variant of sttsm_bcss.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * where they call it — code under a fixed, pre-reserved memory budget

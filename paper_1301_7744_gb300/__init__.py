@@ -81,6 +81,20 @@ def _load():
     L.sttsm_bcss_host.restype = i32
     L.sttsm_device_status.argtypes = []
     L.sttsm_device_status.restype = i32
+    L.sttsm_autotune_b.argtypes = [i32, i64, i64, i32, P, i32]
+    L.sttsm_autotune_b.restype = i32
+    L.sttsm_batch_plan_create.argtypes = [P, i32, i32, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]
+    L.sttsm_batch_plan_create.restype = i32
+    L.sttsm_batch_workspace_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    L.sttsm_batch_workspace_size.restype = i32
+    L.sttsm_batch_info.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.sttsm_batch_info.restype = i32
+    L.sttsm_batch_run.argtypes = [P, P, ctypes.c_size_t, P]
+    L.sttsm_batch_run.restype = i32
+    L.sttsm_batch_plan_destroy.argtypes = [P]
+    L.sttsm_batch_plan_destroy.restype = i32
+    L.sttsm_batch.argtypes = [P, i32, i32, P, ctypes.c_size_t, P]
+    L.sttsm_batch.restype = i32
     L.sttsm_bcss_noalloc.argtypes = [P, P, i32, i64, i64, i32, P, i32, P]
     L.sttsm_bcss_noalloc.restype = i32
     L.sttsm_profile_enable.argtypes = [i32]
@@ -98,7 +112,8 @@ def exported_symbols() -> list[str]:
     return ["bcss_num_blocks", "bcss_num_elems", "bcss_block_rank", "bcss_block_unrank", "sttsm_flops",
             "bcss_pack", "bcss_unpack", "sttsm_workspace_size", "sttsm_bcss", "sttsm_bcss_host",
             "sttsm_device_status", "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read",
-            "sttsm_bcss_noalloc"]
+            "sttsm_bcss_noalloc", "sttsm_autotune_b", "sttsm_batch_plan_create", "sttsm_batch_workspace_size",
+            "sttsm_batch_info", "sttsm_batch_run", "sttsm_batch_plan_destroy", "sttsm_batch"]
 
 
 def _check(fn: str, rc: int) -> None:
@@ -227,6 +242,74 @@ def sttsm_bcss_host(A, X, m: int, n: int, p: int, b: int, C, prec: int, dA, dX, 
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("sttsm_bcss_host", _load().sttsm_bcss_host(_hptr(A), _hptr(X), m, n, p, b, _hptr(C), prec,
                                                       _dptr(dA), _dptr(dX), _dptr(dC), ws, nbytes, _stream(stream)))
+
+
+class SttsmDesc(ctypes.Structure):
+    """sttsm_desc: one instance of a batch (device pointers)."""
+    _fields_ = [("A", ctypes.c_void_p), ("X", ctypes.c_void_p), ("C", ctypes.c_void_p), ("m", ctypes.c_int),
+                ("n", ctypes.c_int64), ("p", ctypes.c_int64), ("b", ctypes.c_int)]
+
+
+def sttsm_autotune_b(m: int, n: int, p: int, prec: int, cands=(4, 8, 16)) -> int:
+    arr = (ctypes.c_int * len(cands))(*cands)
+    rc = _load().sttsm_autotune_b(m, n, p, prec, arr, len(cands))
+    if rc <= 0:
+        raise SttsmError("sttsm_autotune_b", rc)
+    return int(rc)
+
+
+def _descs(instances):
+    """instances: iterables of (A, X, C, m, n, p, b) with CUDA tensors."""
+    arr = (SttsmDesc * len(instances))()
+    for i, (A, X, C, m, n, p, b) in enumerate(instances):
+        arr[i] = SttsmDesc(_dptr(A).value, _dptr(X).value, _dptr(C).value, m, n, p, b)
+    return arr
+
+
+class BatchPlan:
+    """sttsm_batch_plan_*: plan once, run (graph replay) many times."""
+
+    def __init__(self, instances, prec: int, ws_budget: int = 0):
+        self._keep = list(instances)
+        arr = _descs(self._keep)
+        h = ctypes.c_void_p(0)
+        _check("sttsm_batch_plan_create", _load().sttsm_batch_plan_create(arr, len(self._keep), prec, ws_budget,
+                                                                          ctypes.byref(h)))
+        self.handle = h
+        self.prec = prec
+
+    def workspace_size(self) -> int:
+        out = ctypes.c_size_t(0)
+        _check("sttsm_batch_workspace_size", _load().sttsm_batch_workspace_size(self.handle, ctypes.byref(out)))
+        return int(out.value)
+
+    def info(self) -> dict:
+        w, f = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check("sttsm_batch_info", _load().sttsm_batch_info(self.handle, ctypes.byref(w), ctypes.byref(f)))
+        return {"waves": w.value, "useful_flops": f.value}
+
+    def run(self, workspace, stream=None) -> None:
+        nbytes = workspace.numel() * workspace.element_size()
+        _check("sttsm_batch_run", _load().sttsm_batch_run(self.handle, ctypes.c_void_p(workspace.data_ptr()), nbytes,
+                                                          _stream(stream)))
+
+    def destroy(self) -> None:
+        if self.handle:
+            _load().sttsm_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sttsm_batch(instances, prec: int, workspace, stream=None) -> None:
+    arr = _descs(list(instances))
+    nbytes = workspace.numel() * workspace.element_size()
+    _check("sttsm_batch", _load().sttsm_batch(arr, len(arr), prec, ctypes.c_void_p(workspace.data_ptr()), nbytes,
+                                              _stream(stream)))
 
 
 def sttsm_device_status() -> int:

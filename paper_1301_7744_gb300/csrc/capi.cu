@@ -135,13 +135,15 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn()
 
 namespace sttsm {
 
-int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp)
+int* batch_status_word() { return status_dev(); }
+
+int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp, int box_rows)
 {
     auto enc = get_encode_fn();
     if (!enc) return STTSM_ERR_CUDA;
     cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)npiece};
     cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
-    cuuint32_t box[3] = {(cuuint32_t)TC_KC, (cuuint32_t)TC_BN, (cuuint32_t)npiece};
+    cuuint32_t box[3] = {(cuuint32_t)TC_KC, (cuuint32_t)box_rows, (cuuint32_t)npiece};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(xpieces), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -272,7 +274,7 @@ int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_
     if (rc != STTSM_OK) return rc;
     if (d < 0 || d >= m) return STTSM_ERR_ARG;
     const bool fp64 = prec == STTSM_FP64;
-    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : TC_BN;
+    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : (tc_small_mode(s) ? TC_SMALL_BN : TC_BN);
     std::vector<Tile> tl;
     std::vector<int32_t> g;
     build_level_tiles(s, d, BM, BN, 0, tl);
@@ -313,7 +315,8 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
     if (take_status() != 0) return STTSM_ERR_TIMEOUT;
     cudaStream_t stream = (cudaStream_t)stream_;
     const bool fp64 = prec == STTSM_FP64;
-    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : TC_BN;
+    const bool small = !fp64 && tc_small_mode(s);
+    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : (small ? TC_SMALL_BN : TC_BN);
     const DevPlan* P = get_dev_plan(m, n, p, b, BM, BN);
     if (!P) return STTSM_ERR_NOMEM;
     char* ws = (char*)workspace;
@@ -328,7 +331,7 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
             rc = cuda_err(launch_split_x((const float*)X, ws + w.xpieces, (int)p, (int)n, w.rows, w.Kp, np, stream));
         }
         if (rc != STTSM_OK) return rc;
-        rc = make_x_tensor_map(&ti.tmX, ws + w.xpieces, np, w.rows, w.Kp);
+        rc = make_x_tensor_map(&ti.tmX, ws + w.xpieces, np, w.rows, w.Kp, BN);
         if (rc != STTSM_OK) return rc;
     }
     for (int d = 0; d < m; ++d) {
@@ -337,6 +340,7 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
         L.parent = d == 0 ? A : bufs[(d - 1) & 1];
         L.out = d == m - 1 ? C : bufs[d & 1];
         L.G = P->d_G[d];
+        L.OFF = P->d_G[d] + level_G_size(s, d);
         L.X = X;
         L.m = m; L.b = b; L.k = LS.k; L.nbar = (int32_t)s.nbar;
         L.n = (int32_t)n; L.p = (int32_t)p;
@@ -351,6 +355,7 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
         const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
         ProfScope ps(stream, fp64 ? 0 : 1, d, lflops);
         if (fp64) rc = cuda_err(launch_level_fp64(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
+        else if (small) rc = cuda_err(launch_level_tc_small(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
         else rc = cuda_err(launch_level_tc(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
         if (rc != STTSM_OK) return rc;
     }

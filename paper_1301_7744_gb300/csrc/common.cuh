@@ -67,6 +67,7 @@ struct LevelInst {
     const void* parent;     // T^(k+1) storage: [parent node][stored block][b^m]
     void* out;              // T^(k) storage:   [child node][stored block][b^m]
     const int32_t* G;       // [P_out][nbar]: (rank of sort(prefix + ibar)) << 3 | insertion position q
+    const int32_t* OFF;     // [k+1][R]: off_q(rr) (below); OFF[k][rr] is also the output row offset
     const void* X;          // FP64 path: X (p x n column-major); split path: unused
     int32_t m, b, k, nbar;
     int32_t n, p;           // unpadded sizes (bounds of X)
@@ -84,7 +85,8 @@ struct LevelInst {
 // and the gathered operand entry for contraction index kk = ibar * b + a is
 //     parent[(parent_node * P_parent + rank) * b^m + off_q(rr) + a * b^q],
 //     off_q(rr) = rr % b^q + b^(q+1) * (rr / b^q),
-// where (rank, q) = G[pr][ibar]: the stored block of the sorted tuple and the
+// (tabulated per level as OFF[q][rr], so kernels do no integer division per
+// entry), where (rank, q) = G[pr][ibar]: the stored block of the sorted tuple and the
 // local mode the contraction index occupies in it (inserting ibar before the
 // first prefix entry >= ibar).  The output entry (rr, c) of child jbar goes to
 //     out[(child_node * P_out + pr) * b^m + rr % b^k + b^k * c + b^(k+1) * (rr / b^k)],

@@ -161,7 +161,7 @@ level_fp64_kernel(const LevelInst* __restrict__ insts, LevelInst inst0, const Ti
                     const int q = g & 7;
                     const int64_t rank = g >> 3;
                     const int bq = I.bpow[q];
-                    const int64_t off = (lrr % bq) + (int64_t)bq * I.b * (lrr / bq) + (int64_t)a * bq;
+                    const int64_t off = I.OFF[q * I.R + lrr] + (int64_t)a * bq;
                     v = parent[rank * I.bm + off];
                 }
                 As[lk0 + e][lr] = v;
@@ -191,7 +191,7 @@ level_fp64_kernel(const LevelInst* __restrict__ insts, LevelInst inst0, const Ti
             const int64_t g = (int64_t)t.row0 + ty * 4 + i;
             if (g >= I.rows_per_parent) continue;
             const int pr = (int)(g / I.R), rr = (int)(g % I.R);
-            const int64_t rowoff = (rr % bk) + (int64_t)bk * I.b * (rr / bk);
+            const int64_t rowoff = I.OFF[I.k * I.R + rr];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int col = tx * 4 + j;

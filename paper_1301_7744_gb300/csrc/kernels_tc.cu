@@ -41,6 +41,7 @@
 // status 1, stops, drains, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda.h>
+#include <mutex>
 #include "common.cuh"
 #include "launch.h"
 
@@ -196,7 +197,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
 struct GatherRow {
     const float* pbase;      // parent node base
     const int32_t* Grow;     // G row of the thread's output prefix block
-    int rr;                  // row inside the output block
+    const int32_t* OFFrow;   // OFF + rr: off_q(rr) at OFFrow[q * R]
     bool valid;
 };
 
@@ -216,7 +217,7 @@ __device__ __forceinline__ void gather8(const GatherRow& R, const LevelInst& I, 
         const int32_t gq = __ldg(R.Grow + ib);
         const int q = gq & 7;
         const int bq = I.bpow[q];
-        const float* src = R.pbase + (int64_t)(gq >> 3) * I.bm + (R.rr % bq) + (int64_t)bq * b * (R.rr / bq) + (int64_t)a * bq;
+        const float* src = R.pbase + (int64_t)(gq >> 3) * I.bm + __ldg(R.OFFrow + q * I.R) + (int64_t)a * bq;
         if (q == 0 && ((uintptr_t)src & 15) == 0) {
             const float4 x0 = __ldg((const float4*)src), x1 = __ldg((const float4*)src + 1);
             v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
@@ -227,39 +228,60 @@ __device__ __forceinline__ void gather8(const GatherRow& R, const LevelInst& I, 
         }
         return;
     }
-    // general case: the 8 entries cross block boundaries (b < 8 or unaligned)
+    // the 8 entries cross block boundaries (b < 8 or unaligned start)
     const float* src = R.pbase;
-    int64_t stride = 0;
+    int stride = 0;
     bool live = false;
-    auto seg = [&]() {
-        live = ib < I.nbar;
-        if (live) {
-            const int32_t gq = __ldg(R.Grow + ib);
-            const int q = gq & 7;
-            const int bq = I.bpow[q];
-            stride = bq;
-            src = R.pbase + (int64_t)(gq >> 3) * I.bm + (R.rr % bq) + (int64_t)bq * b * (R.rr / bq) + (int64_t)a * bq;
-        }
-    };
-    seg();
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
+        if (e == 0 || a == 0) {
+            live = ib < I.nbar;
+            if (live) {
+                const int32_t gq = __ldg(R.Grow + ib);
+                const int q = gq & 7;
+                stride = I.bpow[q];
+                src = R.pbase + (int64_t)(gq >> 3) * I.bm + __ldg(R.OFFrow + q * I.R) + (int64_t)a * stride;
+            }
+        }
         v[e] = live ? __ldg(src) : 0.f;
-        if (live) src += stride;
-        if (++a == b) { a = 0; ++ib; seg(); }
+        src += stride;
+        if (++a == b) { a = 0; ++ib; }
     }
 }
 
 __device__ __forceinline__ GatherRow gather_row(const Tile& t, const LevelInst& I, int row)
 {
     GatherRow R;
-    const int64_t g = (int64_t)t.row0 + row;
+    const int g = t.row0 + row;
     R.valid = g < I.rows_per_parent;
-    const int pr = R.valid ? (int)(g / I.R) : 0;
-    R.rr = R.valid ? (int)(g % I.R) : 0;
+    const int pr = R.valid ? g / I.R : 0;
+    const int rr = R.valid ? g - pr * I.R : 0;
     R.pbase = (const float*)I.parent + (int64_t)t.parent * I.P_parent * I.bm;
     R.Grow = I.G + (int64_t)pr * I.nbar;
+    R.OFFrow = I.OFF + rr;
     return R;
+}
+
+// Scatter n (<= N) values of one output row into the children's blocks:
+// column c0 + e goes to child (c0 + e) / b, entry (rr, (c0 + e) % b).
+template <int N>
+__device__ __forceinline__ void store_row(const Tile& t, const LevelInst& I, int row, int colbase, const float* vals)
+{
+    const int g = t.row0 + row;
+    if (g >= I.rows_per_parent) return;
+    const int pr = g / I.R, rr = g - pr * I.R;
+    const int b = I.b, bk = I.bpow[I.k];
+    const int64_t rowoff = __ldg(I.OFF + I.k * I.R + rr);
+    const int cg0 = t.col0 + colbase;
+    int jb = cg0 / b, c = cg0 - jb * b;
+    float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
+    const int nvalid = t.ncols - colbase;
+    const int64_t node_stride = I.P_out * I.bm;
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+        if (e < nvalid) dst[(int64_t)bk * c] = vals[e];
+        if (++c == b) { c = 0; dst += node_stride; }
+    }
 }
 
 template <int NP>
@@ -417,23 +439,7 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
             __syncwarp();
             if (lane == 0) mbar_arrive(d1_empty);
             // scatter the row's 64 columns into the children's blocks
-            if (active && valid) {
-                const int64_t g = (int64_t)t.row0 + row;
-                const int pr = (int)(g / I.R), rr = (int)(g % I.R);
-                const int b = I.b;
-                const int bk = I.bpow[I.k];
-                float* out = (float*)I.out;
-                const int64_t rowoff = (rr % bk) + (int64_t)bk * b * (rr / bk);
-                const int cg0 = t.col0 + colbase;
-                int jb = cg0 / b, c = cg0 - jb * b;
-                float* dst = out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
-                const int nvalid = t.ncols - colbase;
-#pragma unroll
-                for (int e = 0; e < 64; ++e) {
-                    if (e < nvalid) dst[(int64_t)bk * c] = acc[e];
-                    if (++c == b) { c = 0; ++jb; dst += I.P_out * I.bm; }
-                }
-            }
+            if (active && valid) store_row<64>(t, I, row, colbase, acc);
         }
         // make sure no TMA write is still in flight before the CTA exits
         if (tma_thread && !ok && last_stage_issued >= 0) {
@@ -518,18 +524,296 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// Small-tile variant for launches whose contraction is short (n̄ b <= 64, at
+// most two stages: one D0 group, so no register running sum is needed) —
+// e.g. batches of small instances.  Tiles are 128 x 64; TMEM holds two tile
+// slots (D1, D0 of 64 columns each) so the MMA runs one tile ahead of the
+// epilogue; 9 warps and ~110 KB of shared memory let two CTAs share an SM.
+//   warps 0-7  workers: rows 32 (w % 4) .. +31; per stage each thread
+//              gathers the 16 contraction entries 16 (w / 4) .. +15 of its
+//              row (two SW64 chunks); the epilogue of tile t-1 runs after the
+//              production of tile t: columns 32 (w / 4) .. +31 of D0 + D1.
+//   warp 8     TMEM allocation and the MMA-issuing thread.
+constexpr int SM_THREADS = 288;
+constexpr int SM_BN = 64;
+
+template <int NP>
+struct SmemSmall {
+    static constexpr int A_PLANE = TC_BM * TC_KC * 2;            // 8 KB
+    static constexpr int B_PLANE = SM_BN * TC_KC * 2;            // 4 KB
+    static constexpr int STAGE = NP * (A_PLANE + B_PLANE);
+    static constexpr int STAGES = 3;
+    static constexpr int BYTES = STAGES * STAGE + 1024 + 256;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(SM_THREADS, 2)
+level_tc_small_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__ insts,
+                      const Tile* __restrict__ tiles, int ntiles, int* status)
+{
+    using S = SmemSmall<NP>;
+    constexpr int STAGES = S::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = (uint64_t*)(smem + STAGES * S::STAGE);
+    // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain
+    uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
+    volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto accf_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
+    auto acce_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 8 * 32 + 1); mbar_init(empty_bar(s), 1); }
+        for (int a = 0; a < 2; ++a) { mbar_init(accf_bar(a), 1); mbar_init(acce_bar(a), 8); }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(smem_u32(tmem_holder)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+    // slot a: D1 at columns 128 a .. +63, D0 at 128 a + 64 .. +63
+
+    if (warp < 8) {
+        // ------------------------------------------------------------ workers
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        const int colbase = half * 32;
+        const bool tma_thread = threadIdx.x == 0;
+        int stage = 0;
+        uint32_t phase = 0, accf_phase = 0;
+        int last_stage_issued = -1;
+        uint32_t last_phase_issued = 0;
+        bool ok = true;
+        float va[8], vb[8];
+
+        // epilogue of the tile pti (slot pit & 1): D0 + D1 -> the children's blocks
+        auto finish = [&](int pti, int pit) -> bool {
+            const int slot = pit & 1;
+            if (!mbar_wait(accf_bar(slot), (accf_phase >> slot) & 1u, abort_flag, status)) return false;
+            accf_phase ^= 1u << slot;
+            tc_fence_after();
+            const Tile t = tiles[pti];
+            const LevelInst& I = (insts ? insts[t.inst] : inst0).L;
+            const bool active = colbase < t.ncols;
+            float out_v[32];
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float d0[8], d1[8];
+                    tmem_ld_32x32b_x8(tmem_base + lane_off + slot * 128 + 64 + colbase + c * 8, d0);
+                    tmem_ld_32x32b_x8(tmem_base + lane_off + slot * 128 + colbase + c * 8, d1);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) out_v[c * 8 + i] = d0[i] + d1[i];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce_bar(slot));
+            if (active) store_row<32>(t, I, row, colbase, out_v);
+            return true;
+        };
+
+        // work items are (tile, stage); the gather of the next item is issued
+        // right after the current one is stored (one call site)
+        int ti = blockIdx.x, ks = 0, it = 0;
+        int prev_ti = -1;
+        Tile t = ti < ntiles ? tiles[ti] : Tile{};
+        const TcInst* TIp = ti < ntiles ? (insts ? insts + t.inst : &inst0) : &inst0;
+        GatherRow GR = gather_row(t, TIp->L, row);
+        int nk = (TIp->L.Ktot + TC_KC - 1) / TC_KC;
+        if (ti < ntiles) {
+            gather8(GR, TIp->L, half * 16, va);
+            gather8(GR, TIp->L, half * 16 + 8, vb);
+        }
+        while (ti < ntiles) {
+            if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+            uint8_t* sA = smem + stage * S::STAGE;
+            uint8_t* sB = sA + NP * S::A_PLANE;
+            if (tma_thread) {
+                mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(NP * S::B_PLANE));
+                tma_load_3d(smem_u32(sB), &TIp->tmX, ks * TC_KC, t.col0, 0, full_bar(stage));
+                last_stage_issued = stage;
+                last_phase_issued = phase;
+            }
+#pragma unroll
+            for (int hc = 0; hc < 2; ++hc) {
+                float* v = hc ? vb : va;
+                const int cq = half * 2 + hc;
+                const uint32_t addr0 = smem_u32(sA) + row * 64 + ((cq ^ ((row >> 1) & 3)) << 4);
+#pragma unroll
+                for (int pc = 0; pc < NP; ++pc) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const __nv_bfloat16 b0 = __float2bfloat16_rn(v[2 * h]), b1 = __float2bfloat16_rn(v[2 * h + 1]);
+                        w[h] = pack_bf16x2(b0, b1);
+                        v[2 * h] -= __bfloat162float(b0);
+                        v[2 * h + 1] -= __bfloat162float(b1);
+                    }
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                                 :: "r"(addr0 + pc * S::A_PLANE), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(full_bar(stage));
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            // advance to the next item and issue its gather
+            const int cur_ti = ti;
+            const bool tile_done = ++ks == nk;
+            if (tile_done) {
+                ti += gridDim.x;
+                ks = 0;
+                if (ti < ntiles) {
+                    t = tiles[ti];
+                    TIp = insts ? insts + t.inst : &inst0;
+                    GR = gather_row(t, TIp->L, row);
+                    nk = (TIp->L.Ktot + TC_KC - 1) / TC_KC;
+                }
+            }
+            if (ti < ntiles) {
+                gather8(GR, TIp->L, ks * TC_KC + half * 16, va);
+                gather8(GR, TIp->L, ks * TC_KC + half * 16 + 8, vb);
+            }
+            if (tile_done) {
+                // the previous tile's epilogue overlaps this tile's MMAs
+                if (prev_ti >= 0 && !finish(prev_ti, it - 1)) { ok = false; break; }
+                prev_ti = cur_ti;
+                ++it;
+            }
+        }
+        if (ok && prev_ti >= 0) ok = finish(prev_ti, it - 1);
+        if (tma_thread && !ok && last_stage_issued >= 0) {
+            uint64_t t0 = globaltimer();
+            while (!mbar_try_wait(full_bar(last_stage_issued), last_phase_issued))
+                if (globaltimer() - t0 > WAIT_LIMIT_NS) break;
+        }
+    } else if (warp == 8) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, acce_phase = 0;
+            bool ok = true, issued = false;
+            int it = 0;
+            for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, ++it) {
+                const Tile t = tiles[ti];
+                const TcInst& TI = insts ? insts[t.inst] : inst0;
+                const int nk = (TI.L.Ktot + TC_KC - 1) / TC_KC;
+                const uint32_t idesc = idesc_bf16((t.ncols + 15) & ~15);
+                const int slot = it & 1;
+                if (!mbar_wait(acce_bar(slot), ((acce_phase >> slot) & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+                acce_phase ^= 1u << slot;
+                tc_fence_after();
+                const uint32_t d1 = tmem_base + slot * 128, d0 = d1 + 64;
+                for (int ks = 0; ks < nk; ++ks) {
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sA = smem_u32(smem + stage * S::STAGE);
+                    const uint32_t sB = sA + NP * S::A_PLANE;
+#pragma unroll
+                    for (int kh = 0; kh < TC_KC / 16; ++kh) {
+#pragma unroll
+                        for (int s = 0; s < NP; ++s) {
+#pragma unroll
+                            for (int u = 0; u < NP; ++u) {
+                                if (s + u > NP - 1) continue;
+                                const uint64_t ad = smem_desc_sw64(sA + s * S::A_PLANE + kh * 32);
+                                const uint64_t bd = smem_desc_sw64(sB + u * S::B_PLANE + kh * 32);
+                                const bool first = ks == 0 && kh == 0 && (s + u == 0 || (s == 0 && u == 1));
+                                tc_mma(s + u == 0 ? d0 : d1, ad, bd, idesc, first ? 0u : 1u);
+                                issued = true;
+                            }
+                        }
+                    }
+                    tc_commit(empty_bar(stage));
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                tc_commit(accf_bar(slot));
+            }
+            if (!ok && issued) {
+                tc_commit(drain_bar);
+                uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(drain_bar, 0))
+                    if (globaltimer() - t0 > WAIT_LIMIT_NS) break;
+            }
+        }
+        __syncwarp();
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 8) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem_base));
+    }
+}
+
+int launch_level_tc_small(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
+                          int num_sms, int* d_status, cudaStream_t s)
+{
+    if (ntiles <= 0) return 0;
+    const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
+    static std::mutex mu;
+    static bool attr_set[2][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 0 && dev < 64 && !attr_set[npiece - 2][dev]) {
+            cudaError_t e = npiece == 3
+                ? cudaFuncSetAttribute(level_tc_small_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemSmall<3>::BYTES)
+                : cudaFuncSetAttribute(level_tc_small_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemSmall<2>::BYTES);
+            if (e != cudaSuccess) return (int)e;
+            attr_set[npiece - 2][dev] = true;
+        }
+    }
+    if (npiece == 3)
+        level_tc_small_kernel<3><<<grid, SM_THREADS, SmemSmall<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
+    else
+        level_tc_small_kernel<2><<<grid, SM_THREADS, SmemSmall<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
+    return (int)cudaGetLastError();
+}
+
 int launch_level_tc(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
                     int num_sms, int* d_status, cudaStream_t s)
 {
     if (ntiles <= 0) return 0;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
+    // the shared-memory opt-in is set once per device (never inside a stream capture after the first call)
+    static std::mutex mu;
+    static bool attr_set[2][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 0 && dev < 64 && !attr_set[npiece - 2][dev]) {
+            cudaError_t e = npiece == 3
+                ? cudaFuncSetAttribute(level_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<3>::BYTES)
+                : cudaFuncSetAttribute(level_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<2>::BYTES);
+            if (e != cudaSuccess) return (int)e;
+            attr_set[npiece - 2][dev] = true;
+        }
+    }
     if (npiece == 3) {
-        cudaError_t e = cudaFuncSetAttribute(level_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<3>::BYTES);
-        if (e != cudaSuccess) return (int)e;
         level_tc_kernel<3><<<grid, NUM_THREADS, Smem<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
     } else if (npiece == 2) {
-        cudaError_t e = cudaFuncSetAttribute(level_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<2>::BYTES);
-        if (e != cudaSuccess) return (int)e;
         level_tc_kernel<2><<<grid, NUM_THREADS, Smem<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
     } else {
         return (int)cudaErrorInvalidValue;

@@ -29,7 +29,14 @@ constexpr int TC_KC = 32;
 int launch_level_tc(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
                     int num_sms, int* d_status, cudaStream_t s);
 
-// Builds the TMA descriptor of an X-piece array.
-int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp);
+// Small-tile variant: every tile has a contraction of at most TC_SMALL_K
+// (two stages) and at most TC_SMALL_BN columns; X maps with box rows 64.
+constexpr int TC_SMALL_K = 64;
+constexpr int TC_SMALL_BN = 64;
+int launch_level_tc_small(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
+                          int num_sms, int* d_status, cudaStream_t s);
+
+// Builds the TMA descriptor of an X-piece array (box: TC_KC x box_rows x npiece).
+int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp, int box_rows = TC_BN);
 
 }  // namespace sttsm

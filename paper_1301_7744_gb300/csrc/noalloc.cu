@@ -65,7 +65,8 @@ extern "C" int sttsm_bcss_noalloc(const void* A, const void* X, int m, int64_t n
 
     // level plans on the host
     const bool fp64 = prec == STTSM_FP64;
-    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : TC_BN;
+    const bool small = !fp64 && tc_small_mode(s);
+    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : (small ? TC_SMALL_BN : TC_BN);
     std::vector<Tile> tiles[STTSM_MAX_M];
     std::vector<int32_t> G[STTSM_MAX_M];
     for (int d = 0; d < m; ++d) {
@@ -128,7 +129,7 @@ extern "C" int sttsm_bcss_noalloc(const void* A, const void* X, int m, int64_t n
     memset(&ti, 0, sizeof(ti));
     if (!fp64) {
         if (launch_split_x((const float*)X, base + x_off, (int)p, (int)n, rows, Kp, np, stream) != 0) return STTSM_ERR_CUDA;
-        if (make_x_tensor_map(&ti.tmX, base + x_off, np, rows, Kp) != STTSM_OK) return STTSM_ERR_CUDA;
+        if (make_x_tensor_map(&ti.tmX, base + x_off, np, rows, Kp, BN) != STTSM_OK) return STTSM_ERR_CUDA;
     }
     for (int d = 0; d < m; ++d) {
         const LevelShape& LS = s.lv[d];
@@ -136,6 +137,7 @@ extern "C" int sttsm_bcss_noalloc(const void* A, const void* X, int m, int64_t n
         L.parent = d == 0 ? A : bufs[(d - 1) & 1];
         L.out = d == m - 1 ? C : bufs[d & 1];
         L.G = (const int32_t*)(base + G_off[d]);
+        L.OFF = L.G + level_G_size(s, d);
         L.X = X;
         L.m = m; L.b = b; L.k = LS.k; L.nbar = (int32_t)s.nbar;
         L.n = (int32_t)n; L.p = (int32_t)p;
@@ -150,7 +152,8 @@ extern "C" int sttsm_bcss_noalloc(const void* A, const void* X, int m, int64_t n
         const Tile* dt = (const Tile*)(base + tiles_off[d]);
         const int nt = (int)tiles[d].size();
         int lrc = fp64 ? launch_level_fp64(L, nullptr, dt, nt, sms, stream)
-                       : launch_level_tc(np, ti, nullptr, dt, nt, sms, status, stream);
+                  : small ? launch_level_tc_small(np, ti, nullptr, dt, nt, sms, status, stream)
+                          : launch_level_tc(np, ti, nullptr, dt, nt, sms, status, stream);
         if (lrc != 0) return STTSM_ERR_CUDA;
     }
     return STTSM_OK;

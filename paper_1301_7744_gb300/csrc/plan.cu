@@ -16,7 +16,7 @@ int make_shape(int m, int64_t n, int64_t p, int b, Shape* s)
     s->pbar = (p + b - 1) / b;
     double bmd = 1.0;
     for (int a = 0; a < m; ++a) bmd *= b;
-    if (bmd / b >= 2147483647.0 || bmd > 1.0e12) return STTSM_ERR_UNSUPPORTED;   // b^(m-1) must fit int32
+    if (bmd >= 2147483647.0) return STTSM_ERR_UNSUPPORTED;   // b^m (in-block offsets) must fit int32
     s->bm = 1;
     for (int a = 0; a < m; ++a) s->bm *= b;
     s->R = s->bm / b;
@@ -66,6 +66,13 @@ void build_level_G(const Shape& s, int d, std::vector<int32_t>& G)
             G[(size_t)(pr * s.nbar + ib)] = (int32_t)((rank << 3) | q);
         }
     }
+    // offset table OFF[q][rr] = rr % b^q + b^(q+1) (rr / b^q), q = 0..k, appended after G
+    const size_t base = G.size();
+    G.resize(base + (size_t)(k + 1) * s.R);
+    int64_t bq = 1;
+    for (int q = 0; q <= k; ++q, bq *= s.b)
+        for (int64_t rr = 0; rr < s.R; ++rr)
+            G[base + (size_t)(q * s.R + rr)] = (int32_t)(rr % bq + bq * s.b * (rr / bq));
 }
 
 void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles)

@@ -30,11 +30,18 @@ struct Shape {
 // Returns 0 and fills s, or an sttsm_status for unsupported sizes.
 int make_shape(int m, int64_t n, int64_t p, int b, Shape* s);
 
+// Split-precision launches of a shape whose contraction n̄ b is at most 64
+// use the small-tile kernel (128 x 64 tiles).
+inline bool tc_small_mode(const Shape& s) { return s.nbar * s.b <= 64; }
+
 // Host tile list and G table of level d (appended to the given vectors).
 // Tiles cover, for every parent node, P_out * R rows in steps of BM and the
 // parent's children * b columns in steps of BN.
 void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles);
+// G table of level d ([P_out][nbar]) followed by its offset table OFF
+// ([k+1][R]); level_G_size is the length of the G part.
 void build_level_G(const Shape& s, int d, std::vector<int32_t>& G);
+inline int64_t level_G_size(const Shape& s, int d) { return s.lv[d].P_out * s.nbar; }
 
 struct DevPlan {
     Shape shape;

@@ -163,3 +163,49 @@ def dev_sym_uniform_dense(ptr: int, m: int, n: int, seed: int, dtype: str, strea
     rc = _d().synth_dev_sym_uniform_dense(ctypes.c_void_p(ptr), m, n, seed, code, ctypes.c_void_p(stream))
     if rc != 0:
         raise RuntimeError("synth_dev_sym_uniform_dense failed with CUDA error %d" % rc)
+
+
+def _uniform01(seed: int, count: int, stream: int) -> np.ndarray:
+    """count Uniform[0,1) draws from Philox word 0, counters (t, 0, stream, 0), key (seed, 2)."""
+    ctr = np.zeros((count, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(count, dtype=np.uint32)
+    ctr[:, 2] = stream
+    w = philox4x32_10(ctr, [seed & 0xFFFFFFFF, 2])[:, 0]
+    return w.astype(np.float64) / 4294967296.0
+
+
+def batch_shapes(seed: int, count: int):
+    """Shapes of the batched workload: m in {3,4,5} with weights {.5,.3,.2},
+    n uniform in {8..64}, p uniform in {8..n}.  Returns a list of (m, n, p)."""
+    u = _uniform01(seed, count, 0)
+    v = _uniform01(seed, count, 1)
+    w = _uniform01(seed, count, 2)
+    m = np.where(u < 0.5, 3, np.where(u < 0.8, 4, 5))
+    n = 8 + np.floor(v * 57).astype(int)
+    p = 8 + np.floor(w * (n - 7)).astype(int)
+    return [(int(a), int(b), int(c)) for a, b, c in zip(m, n, p)]
+
+
+SERVE_CLASSES = ((3, 64, 512), (4, 32, 160), (5, 16, 64), (6, 8, 32))
+
+
+def serve_requests(seed: int, rate: float, seconds: float):
+    """Poisson arrivals at `rate` per second over `seconds`; each request is
+    uniform over the four (m, range) classes with n, p uniform in the class
+    range.  Returns a list of (arrival_s, m, n, p)."""
+    expect = int(rate * seconds * 1.2) + 64
+    u = _uniform01(seed, expect, 0)
+    gaps = -np.log1p(-u) / rate
+    t = np.cumsum(gaps)
+    t = t[t < seconds]
+    k = len(t)
+    cls = np.minimum((_uniform01(seed, k, 1) * 4).astype(int), 3)
+    a = _uniform01(seed, k, 2)
+    c = _uniform01(seed, k, 3)
+    out = []
+    for i in range(k):
+        m, lo, hi = SERVE_CLASSES[cls[i]]
+        n = lo + int(a[i] * (hi - lo + 1))
+        p = lo + int(c[i] * (hi - lo + 1))
+        out.append((float(t[i]), m, min(n, hi), min(p, hi)))
+    return out

@@ -98,3 +98,39 @@ def test_workspace_sizes(st):
         st.sttsm_workspace_size(9, 24, 24, 8, st.STTSM_FP64)
     with pytest.raises(st.SttsmError):
         st.sttsm_workspace_size(3, 0, 24, 8, st.STTSM_FP64)
+
+
+def test_autotune_picks_a_candidate(st):
+    for m, n, p in [(3, 20, 12), (4, 64, 40), (5, 33, 33), (3, 768, 768)]:
+        cands = (4, 8, 16) if n < 100 else (32, 48, 64)
+        b = st.sttsm_autotune_b(m, n, p, st.STTSM_BF16X6, cands)
+        assert b in cands
+    # the FP64 path minimises the Tbl. 4 flop count
+    cands = (4, 8, 16)
+    b = st.sttsm_autotune_b(3, 48, 48, st.STTSM_FP64, cands)
+    assert b == min(cands, key=lambda c: st.sttsm_flops(3, 48, 48, c))
+    with pytest.raises(st.SttsmError):
+        st.sttsm_autotune_b(3, 48, 48, st.STTSM_FP64, ())
+
+
+def test_batch_shapes_follow_the_workload_recipe():
+    import collections
+    import synth
+    sh = synth.batch_shapes(3, 4096)
+    cnt = collections.Counter(m for m, _, _ in sh)
+    assert set(cnt) == {3, 4, 5}
+    assert abs(cnt[3] / 4096 - 0.5) < 0.03 and abs(cnt[4] / 4096 - 0.3) < 0.03
+    assert all(8 <= n <= 64 and 8 <= p <= n for _, n, p in sh)
+    assert sh == synth.batch_shapes(3, 4096)
+
+
+def test_serving_arrivals_are_poisson():
+    import synth
+    rq = synth.serve_requests(4, 2000.0, 5.0)
+    t = np.array([r[0] for r in rq])
+    assert abs(len(rq) / 5.0 - 2000) < 150 and np.all(np.diff(t) > 0)
+    gaps = np.diff(t)
+    assert abs(gaps.mean() * 2000 - 1) < 0.05 and abs(gaps.std() / gaps.mean() - 1) < 0.1
+    for _, m, n, p in rq:
+        lo, hi = {3: (64, 512), 4: (32, 160), 5: (16, 64), 6: (8, 32)}[m]
+        assert lo <= n <= hi and lo <= p <= hi

@@ -38,8 +38,12 @@ def emulate(st, m, n, p, b, prec, A_bcss, X):
             assert out_size == st.bcss_num_elems(m, p, b)
         out = np.zeros(out_size)
         count = np.zeros(out_size, dtype=np.int64)
-        G = G.reshape(P_out, nbar)
+        OFF = G[P_out * nbar:].reshape(k + 1, R)
+        G = G[: P_out * nbar].reshape(P_out, nbar)
         assert np.all((G >> 3) < P_par) and np.all((G & 7) <= k)
+        rrs = np.arange(R)
+        for q in range(k + 1):
+            assert np.array_equal(OFF[q], rrs % b ** q + b ** (q + 1) * (rrs // b ** q))
         kk = np.arange(nbar * b)
         ib, a = kk // b, kk % b
         for inst, par, cb, row0, col0, ncols, _, _ in tiles:
@@ -51,7 +55,7 @@ def emulate(st, m, n, p, b, prec, A_bcss, X):
             gq = G[pr[:, None], ib[None, :]]
             q, rank = gq & 7, gq >> 3
             bq = b ** q
-            off = (rr[:, None] % bq) + bq * b * (rr[:, None] // bq) + a[None, :] * bq
+            off = OFF[q, rr[:, None]] + a[None, :] * bq
             assert off.min() >= 0 and off.max() < bm
             idx = (par * P_par + rank) * bm + off
             assert idx.min() >= 0 and idx.max() < parent.size
@@ -60,7 +64,7 @@ def emulate(st, m, n, p, b, prec, A_bcss, X):
             T = parent[idx] @ Xpad[cols, :].T
             jb, c = cols // b, cols % b
             bk = b ** k
-            rowoff = (rr % bk) + bk * b * (rr // bk)
+            rowoff = OFF[k, rr]
             oidx = ((cb + jb)[None, :] * P_out + pr[:, None]) * bm + rowoff[:, None] + bk * c[None, :]
             assert oidx.min() >= 0 and oidx.max() < out_size
             out[oidx] = T
