@@ -56,6 +56,9 @@ def parse_args():
                     help="single: m=3 n=p=768 instance (default); batch: 4096 mixed instances; serve: Poisson stream")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--ws-gb", type=float, default=48.0, help="batch workspace budget (GiB)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="time the headline step only (no e2e, FP64 path, check or CPU baseline); for profiling")
     return ap.parse_args()
@@ -416,8 +419,122 @@ def run_batch(args):
     return 0
 
 
+SERVE_B = {3: (16, 32, 64), 4: (8, 16, 32), 5: (4, 8, 16), 6: (4, 8)}
+
+
+def run_serve(args):
+    """Serving workload: Poisson arrivals (rate, seconds), uniform over the classes
+    m=3 (n,p in [64,512]), m=4 ([32,160]), m=5 ([16,64]), m=6 ([8,32]); BF16X6; the
+    server admits by HBM budget and batches continuously.  Inputs come from a pool of
+    pre-generated instances per class (shapes drawn from the class ranges); each
+    request uses pool entry (class, index mod pool size) with its own output buffer."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_7744_gb300 as st
+    import synth
+    prec = st.STTSM_BF16X6
+    reqs = synth.serve_requests(4, args.serve_rate, args.serve_seconds)
+    pool_n, cbuf = 32, 8
+    rng = np.random.default_rng(11)
+    stream = torch.cuda.current_stream().cuda_stream
+    pool = {}
+    for m, lo, hi in synth.SERVE_CLASSES:
+        entries = []
+        for e in range(pool_n):
+            n, p = int(rng.integers(lo, hi + 1)), int(rng.integers(lo, hi + 1))
+            b = st.sttsm_autotune_b(m, n, p, prec, SERVE_B[m])
+            d = torch.empty(n ** m, dtype=torch.float32, device="cuda")
+            synth.dev_sym_uniform_dense(d.data_ptr(), m, n, 7000 + 100 * m + e, "f32", stream)
+            A = torch.empty(st.bcss_num_elems(m, n, b), dtype=torch.float32, device="cuda")
+            st.bcss_pack(d, A, m, n, b)
+            del d
+            X = torch.from_numpy(xcol32(synth.x_gaussian(8000 + 100 * m + e, p, n))).cuda()
+            Cs = [torch.empty(st.bcss_num_elems(m, p, b), dtype=torch.float32, device="cuda") for _ in range(cbuf)]
+            entries.append(dict(A=A, X=X, C=Cs, m=m, n=n, p=p, b=b, F=st.sttsm_flops(m, n, p, b)))
+        pool[m] = entries
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    srv = st.Server(int(args.serve_budget_gb * 2 ** 30), prec)
+    # warm-up: one request per pool entry (plans, G tables, TMEM/attribute set-up)
+    warm = []
+    for m in pool:
+        for e in pool[m]:
+            warm.append(srv.submit(e["A"], e["X"], e["C"][0], e["m"], e["n"], e["p"], e["b"]))
+    while not all(srv.poll(t)[0] for t in warm):
+        time.sleep(0.001)
+    count = {m: 0 for m in pool}
+    tickets, flops = [], 0.0
+    busy = 0
+    clocks = ClockSampler()
+    clocks.start()
+    t0 = time.perf_counter()
+    max_queue, max_active, max_arena = 0, 0, 0
+    for i, (ta, m, _n, _p) in enumerate(reqs):
+        while True:
+            dt = t0 + ta - time.perf_counter()
+            if dt <= 0:
+                break
+            if dt > 2e-4:
+                time.sleep(dt - 1e-4)
+        e = pool[m][count[m] % pool_n]
+        c = e["C"][(count[m] // pool_n) % cbuf]
+        count[m] += 1
+        while True:
+            try:
+                tickets.append(srv.submit(e["A"], e["X"], c, e["m"], e["n"], e["p"], e["b"]))
+                break
+            except st.SttsmError as err:
+                if err.code != st.STTSM_ERR_BUSY:
+                    raise
+                busy += 1
+                time.sleep(1e-4)
+        flops += e["F"]
+        if i % 256 == 0:
+            sts = srv.stats()
+            max_queue = max(max_queue, sts["queued"])
+            max_active = max(max_active, sts["active"])
+            max_arena = max(max_arena, sts["arena_bytes"])
+    t_sub = time.perf_counter() - t0
+    lat = []
+    pending = list(tickets)
+    while pending:
+        nxt = []
+        for t in pending:
+            done, ms = srv.poll(t)
+            if done:
+                lat.append(ms)
+            else:
+                nxt.append(t)
+        pending = nxt
+        if pending:
+            time.sleep(0.001)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    srv.destroy()
+    lat = np.array(lat)
+    line = {"metric": "sttsm serving latency p50/p99 (ms) and throughput, Poisson %.0f req/s for %.0f s"
+                      % (args.serve_rate, args.serve_seconds),
+            "value": float(np.percentile(lat, 99)), "unit": "ms (p99 latency)", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "bf16x6", "data": "synthetic",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p999_ms": float(np.percentile(lat, 99.9)), "mean_ms": float(lat.mean()),
+            "requests": len(lat), "throughput_req_s": len(lat) / wall, "useful_tflops": flops / wall / 1e12,
+            "submit_seconds": t_sub, "wall_seconds": wall, "busy_retries": busy,
+            "max_queued": max_queue, "max_active": max_active, "max_arena_gb": max_arena / 2 ** 30,
+            "config": {"workload": "Poisson stream, classes m=3 n,p in [64,512]; m=4 [32,160]; m=5 [16,64]; "
+                                   "m=6 [8,32]; b autotuned per pool entry",
+                       "hbm_budget_gb": args.serve_budget_gb, "pool_per_class": pool_n,
+                       "b_candidates": {str(k): v for k, v in SERVE_B.items()}},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

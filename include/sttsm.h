@@ -180,6 +180,35 @@ int sttsm_batch_plan_destroy(void* plan);
 /* One-shot batch: plan, run, synchronise `stream`, destroy. */
 int sttsm_batch(const sttsm_desc* d, int count, int prec, void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------ serving (device) */
+
+/* Continuous-batching server for sttsm requests (split precisions only).
+ * The handle owns an HBM arena of hbm_budget_bytes for the workspaces of
+ * admitted requests, a CUDA stream and a scheduler thread.  Requests wait in
+ * a FIFO queue (at most queue_cap) until their workspace fits in the arena;
+ * each admitted request advances one level of Fig. 5 per step, and one step
+ * covers every active request at its own level in shared launches, so
+ * requests arriving while others run overlap with them on the device.
+ * A, X and C stay where the caller put them (device memory, BCSS); the
+ * caller keeps them valid until the request is done. */
+int sttsm_serve_create(size_t hbm_budget_bytes, int prec, int queue_cap, void** handle);
+
+/* Queues one request.  STTSM_ERR_BUSY if the queue is full, STTSM_ERR_NOMEM
+ * if its workspace alone exceeds the budget. */
+int sttsm_serve_submit(void* handle, const sttsm_desc* d, uint64_t* ticket);
+
+/* done = 1 once C is complete; latency_ms = completion (seen by the
+ * scheduler) minus submission, host clock.  Returns STTSM_ERR_TIMEOUT if a
+ * device-side wait timed out, or the scheduler's error. */
+int sttsm_serve_poll(void* handle, uint64_t ticket, int* done, double* latency_ms);
+
+/* out[6]: submitted, admitted, completed, queued, active, arena bytes in use. */
+int sttsm_serve_stats(void* handle, uint64_t* out);
+
+/* Stops the scheduler, waits for the stream, frees the handle.  Requests not
+ * yet done are dropped (their C is undefined). */
+int sttsm_serve_destroy(void* handle);
+
 /* Allocation-free variant of sttsm_bcss.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * where they call it — code under a fixed, pre-reserved memory budget

@@ -95,6 +95,16 @@ def _load():
     L.sttsm_batch_plan_destroy.restype = i32
     L.sttsm_batch.argtypes = [P, i32, i32, P, ctypes.c_size_t, P]
     L.sttsm_batch.restype = i32
+    L.sttsm_serve_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(ctypes.c_void_p)]
+    L.sttsm_serve_create.restype = i32
+    L.sttsm_serve_submit.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+    L.sttsm_serve_submit.restype = i32
+    L.sttsm_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.sttsm_serve_poll.restype = i32
+    L.sttsm_serve_stats.argtypes = [P, P]
+    L.sttsm_serve_stats.restype = i32
+    L.sttsm_serve_destroy.argtypes = [P]
+    L.sttsm_serve_destroy.restype = i32
     L.sttsm_bcss_noalloc.argtypes = [P, P, i32, i64, i64, i32, P, i32, P]
     L.sttsm_bcss_noalloc.restype = i32
     L.sttsm_profile_enable.argtypes = [i32]
@@ -113,7 +123,8 @@ def exported_symbols() -> list[str]:
             "bcss_pack", "bcss_unpack", "sttsm_workspace_size", "sttsm_bcss", "sttsm_bcss_host",
             "sttsm_device_status", "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read",
             "sttsm_bcss_noalloc", "sttsm_autotune_b", "sttsm_batch_plan_create", "sttsm_batch_workspace_size",
-            "sttsm_batch_info", "sttsm_batch_run", "sttsm_batch_plan_destroy", "sttsm_batch"]
+            "sttsm_batch_info", "sttsm_batch_run", "sttsm_batch_plan_destroy", "sttsm_batch", "sttsm_serve_create",
+            "sttsm_serve_submit", "sttsm_serve_poll", "sttsm_serve_stats", "sttsm_serve_destroy"]
 
 
 def _check(fn: str, rc: int) -> None:
@@ -310,6 +321,45 @@ def sttsm_batch(instances, prec: int, workspace, stream=None) -> None:
     nbytes = workspace.numel() * workspace.element_size()
     _check("sttsm_batch", _load().sttsm_batch(arr, len(arr), prec, ctypes.c_void_p(workspace.data_ptr()), nbytes,
                                               _stream(stream)))
+
+
+class Server:
+    """sttsm_serve_*: continuous-batching server under an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes: int, prec: int = STTSM_BF16X6, queue_cap: int = 1 << 20):
+        h = ctypes.c_void_p(0)
+        _check("sttsm_serve_create", _load().sttsm_serve_create(hbm_budget_bytes, prec, queue_cap, ctypes.byref(h)))
+        self.handle = h
+        self.prec = prec
+
+    def submit(self, A, X, C, m: int, n: int, p: int, b: int) -> int:
+        """Queues C := [A; X, ..., X]; returns a ticket.  Raises SttsmError (code STTSM_ERR_BUSY) if full."""
+        d = SttsmDesc(_dptr(A).value, _dptr(X).value, _dptr(C).value, m, n, p, b)
+        t = ctypes.c_uint64(0)
+        _check("sttsm_serve_submit", _load().sttsm_serve_submit(self.handle, ctypes.byref(d), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(done, latency_ms)."""
+        done, lat = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check("sttsm_serve_poll", _load().sttsm_serve_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(lat)))
+        return bool(done.value), float(lat.value)
+
+    def stats(self) -> dict:
+        out = (ctypes.c_uint64 * 6)()
+        _check("sttsm_serve_stats", _load().sttsm_serve_stats(self.handle, out))
+        return dict(zip(["submitted", "admitted", "completed", "queued", "active", "arena_bytes"], [int(v) for v in out]))
+
+    def destroy(self) -> None:
+        if self.handle:
+            _load().sttsm_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def sttsm_device_status() -> int:

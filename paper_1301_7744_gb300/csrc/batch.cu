@@ -53,35 +53,6 @@ double plan_cost(const Shape& s, int prec, int BM, int BN)
     return c;
 }
 
-struct SplitDesc {
-    const float* X;
-    void* out;
-    int p, n, rows, Kp;
-    int64_t first_block;   // first CTA of this instance in the batched split launch
-};
-
-__global__ void split_x_batch_kernel(const SplitDesc* __restrict__ d, int count, int npiece)
-{
-    // find this CTA's instance: last descriptor with first_block <= blockIdx.x
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (d[mid].first_block <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
-    }
-    const SplitDesc D = d[lo];
-    const int64_t total = (int64_t)D.rows * D.Kp;
-    const int64_t t = ((int64_t)blockIdx.x - D.first_block) * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const int j = (int)(t / D.Kp), i = (int)(t % D.Kp);
-    float v = (j < D.p && i < D.n) ? D.X[j + (int64_t)i * D.p] : 0.f;
-    __nv_bfloat16* out = (__nv_bfloat16*)D.out;
-    for (int pc = 0; pc < npiece; ++pc) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        out[pc * total + t] = h;
-        v = v - __bfloat162float(h);
-    }
-}
-
 struct Instance {
     sttsm_desc desc;
     Shape shape;
@@ -230,8 +201,7 @@ int enqueue(sttsm_batch_plan_s* P, cudaStream_t s)
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
     for (Wave& w : P->waves) {
         if (!fp64 && w.split_blocks > 0) {
-            split_x_batch_kernel<<<w.split_blocks, 256, 0, s>>>(w.d_split, (int)w.ids.size(), np);
-            if (cudaGetLastError() != cudaSuccess) return STTSM_ERR_CUDA;
+            if (launch_split_x_batch(w.d_split, (int)w.ids.size(), w.split_blocks, np, s) != 0) return STTSM_ERR_CUDA;
         }
         for (int d = 0; d < w.max_m; ++d)
         for (int mode = 0; mode < 2; ++mode) {

@@ -136,6 +136,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn()
 namespace sttsm {
 
 int* batch_status_word() { return status_dev(); }
+int peek_status_word() { return g_status_host ? __atomic_load_n(g_status_host, __ATOMIC_SEQ_CST) : 0; }
 
 int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp, int box_rows)
 {

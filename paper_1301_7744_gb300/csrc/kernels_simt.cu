@@ -118,6 +118,35 @@ int launch_split_x(const float* X, void* out, int p, int n, int rows, int Kp, in
     return (int)cudaGetLastError();
 }
 
+__global__ void split_x_batch_kernel(const SplitDesc* __restrict__ d, int count, int npiece)
+{
+    // this CTA's instance: the last descriptor with first_block <= blockIdx.x
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (d[mid].first_block <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const SplitDesc D = d[lo];
+    const int64_t total = (int64_t)D.rows * D.Kp;
+    const int64_t t = ((int64_t)blockIdx.x - D.first_block) * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int j = (int)(t / D.Kp), i = (int)(t % D.Kp);
+    float v = (j < D.p && i < D.n) ? D.X[j + (int64_t)i * D.p] : 0.f;
+    __nv_bfloat16* out = (__nv_bfloat16*)D.out;
+    for (int pc = 0; pc < npiece; ++pc) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        out[pc * total + t] = h;
+        v = v - __bfloat162float(h);
+    }
+}
+
+int launch_split_x_batch(const SplitDesc* d_desc, int count, int blocks, int npiece, cudaStream_t s)
+{
+    if (count <= 0 || blocks <= 0) return 0;
+    split_x_batch_kernel<<<blocks, 256, 0, s>>>(d_desc, count, npiece);
+    return (int)cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ FP64 level kernel
 
 // Tile of 64 output rows x 64 output columns, 256 threads, each thread 4x4

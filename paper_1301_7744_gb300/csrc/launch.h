@@ -17,6 +17,15 @@ struct TcInst {   // CUtensorMap first: inherits its 64-byte alignment
 int launch_bcss_pack(const void* dense, void* bcss, int m, int64_t n, int b, int dtype, cudaStream_t s);
 int launch_bcss_unpack(const void* bcss, void* dense, int m, int64_t n, int b, int dtype, cudaStream_t s);
 int launch_split_x(const float* X, void* out, int p, int n, int rows, int Kp, int npiece, cudaStream_t s);
+
+// Batched X split: instance i owns CTAs [first_block, first_block + ceil(rows * Kp / 256)).
+struct SplitDesc {
+    const float* X;
+    void* out;
+    int p, n, rows, Kp;
+    int64_t first_block;
+};
+int launch_split_x_batch(const SplitDesc* d_desc, int count, int blocks, int npiece, cudaStream_t s);
 int launch_level_fp64(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
                       int num_sms, cudaStream_t s);
 

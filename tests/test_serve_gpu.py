@@ -1,0 +1,125 @@
+"""Continuous-batching server: requests of mixed sizes submitted while others
+run must give the same C as the same request run alone (same tiles, same
+arithmetic: bit for bit), and the oracle's within the split-path tolerance;
+admission waits for workspace under the HBM budget; a full queue says BUSY
+and an over-budget request says NOMEM — all decided on the host."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import device_bcss_from_dense, oracle_C_bcss, rel_fro, xcol
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CLASSES = {3: (64, 112), 4: (32, 48), 5: (16, 24), 6: (8, 12)}   # sizes kept oracle-friendly
+
+
+@pytest.fixture(scope="module")
+def st():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_7744_gb300 as pkg
+    return pkg
+
+
+def make_request(st, i, m, n, p):
+    cands = {3: (16, 32), 4: (8, 16), 5: (4, 8), 6: (4, 8)}[m]
+    b = st.sttsm_autotune_b(m, n, p, st.STTSM_BF16X6, cands)
+    A = synth.sym_uniform_dense(m, n, 300 + i)
+    X = synth.x_gaussian(400 + i, p, n).astype(np.float32).astype(np.float64)
+    Ab = device_bcss_from_dense(st, A, m, n, b, torch.float32)
+    dX = torch.from_numpy(xcol(X)).to(device="cuda", dtype=torch.float32)
+    C = torch.full((st.bcss_num_elems(m, p, b),), float("nan"), dtype=torch.float32, device="cuda")
+    return dict(A=A, X=X, Ab=Ab, dX=dX, C=C, m=m, n=n, p=p, b=b)
+
+
+def requests(st, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = [3, 4, 5, 6][i % 4]
+        lo, hi = CLASSES[m]
+        out.append(make_request(st, seed * 1000 + i, m, int(rng.integers(lo, hi + 1)), int(rng.integers(lo, hi + 1))))
+    return out
+
+
+def wait_all(srv, tickets, timeout=120.0):
+    t0 = time.time()
+    lat = {}
+    while len(lat) < len(tickets):
+        for t in tickets:
+            if t not in lat:
+                done, ms = srv.poll(t)
+                if done:
+                    lat[t] = ms
+        assert time.time() - t0 < timeout, "requests did not complete"
+        time.sleep(0.001)
+    return lat
+
+
+def alone(st, r):
+    C = torch.empty_like(r["C"])
+    st.sttsm_bcss(r["Ab"], r["dX"], r["m"], r["n"], r["p"], r["b"], C, st.STTSM_BF16X6,
+                  st.workspace_tensor(r["m"], r["n"], r["p"], r["b"], st.STTSM_BF16X6))
+    torch.cuda.synchronize()
+    return C.double().cpu().numpy()
+
+
+def test_mixed_requests_equal_alone_and_oracle(st):
+    reqs = requests(st, 24, 1)
+    torch.cuda.synchronize()
+    srv = st.Server(2 << 30)
+    tickets = []
+    for k, r in enumerate(reqs):                 # three bursts: later ones join running steps
+        tickets.append(srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"]))
+        if k % 8 == 7:
+            time.sleep(0.002)
+    lat = wait_all(srv, tickets)
+    assert all(v > 0 for v in lat.values())
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs) and stats["queued"] == 0 and stats["active"] == 0
+    assert stats["arena_bytes"] == 0
+    srv.destroy()
+    for k, r in enumerate(reqs):
+        got = r["C"].double().cpu().numpy()
+        assert np.array_equal(got, alone(st, r)), k
+        if k % 3 == 0:
+            assert rel_fro(got, oracle_C_bcss(r["A"], r["X"], r["m"], r["p"], r["b"])) <= 1e-6
+
+
+def test_admission_waits_under_a_tight_budget(st):
+    reqs = requests(st, 12, 2)
+    need = max(st.sttsm_workspace_size(r["m"], r["n"], r["p"], r["b"], st.STTSM_BF16X6) for r in reqs)
+    srv = st.Server(need + need // 2)            # room for about one request at a time
+    tickets = [srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"]) for r in reqs]
+    peak_queue = srv.stats()["queued"]
+    wait_all(srv, tickets)
+    srv.destroy()
+    assert peak_queue >= 1
+    for r in reqs:
+        assert np.array_equal(r["C"].double().cpu().numpy(), alone(st, r))
+
+
+def test_busy_queue_and_over_budget_request(st):
+    big = make_request(st, 9000, 3, 400, 400)
+    small = [make_request(st, 9001 + i, 5, 16, 16) for i in range(4)]
+    need = st.sttsm_workspace_size(big["m"], big["n"], big["p"], big["b"], st.STTSM_BF16X6)
+    srv = st.Server(need, queue_cap=2)
+    t_big = srv.submit(big["Ab"], big["dX"], big["C"], big["m"], big["n"], big["p"], big["b"])
+    codes = []                                    # the big request holds the whole arena for ~1 ms
+    for r in small:
+        try:
+            srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"])
+            codes.append(0)
+        except st.SttsmError as e:
+            codes.append(e.code)
+    huge = make_request(st, 9100, 3, 512, 512)
+    with pytest.raises(st.SttsmError) as e:
+        srv.submit(huge["Ab"], huge["dX"], huge["C"], huge["m"], huge["n"], huge["p"], huge["b"])
+    assert e.value.code == st.STTSM_ERR_NOMEM
+    wait_all(srv, [t_big])
+    srv.destroy()
+    assert st.STTSM_ERR_BUSY in codes and 0 in codes
