@@ -92,21 +92,27 @@ int npiece_of(int prec)
     return 0;
 }
 
-// Workspace layout: [X pieces (split precisions)][temporaries buffer 0][buffer 1].
+// Workspace layout: [X pieces (split precisions)][A pieces (TMA-fed kernel)]
+// [temporaries buffer 0][buffer 1]; the TMA-fed kernel keeps temporaries as
+// NP BF16 pieces per entry, the other paths as FP32 / FP64.
 struct WsLayout {
-    size_t xpieces, buf0, buf1, total;
+    size_t xpieces, apieces, buf0, buf1, total;
     int rows, Kp;
+    bool tma;
 };
 
 WsLayout ws_layout(const Shape& s, int prec)
 {
     WsLayout w;
-    const size_t esz = prec == STTSM_FP64 ? 8 : 4;
     const int np = npiece_of(prec);
+    w.tma = np && tc_tma_mode(s);
+    const size_t esz = prec == STTSM_FP64 ? 8 : (w.tma ? 2 * (size_t)np : 4);
     w.rows = (int)(s.pbar * s.b);
     w.Kp = (int)(((s.nbar * s.b) + 7) / 8 * 8);
     w.xpieces = 0;
     size_t off = np ? align256((size_t)np * w.rows * w.Kp * 2) : 0;
+    w.apieces = off;
+    if (w.tma) off += align256((size_t)np * s.lv[0].P_parent * s.bm * 2);
     w.buf0 = off;
     off += align256((size_t)s.buf_elems[0] * esz);
     w.buf1 = off;
@@ -137,6 +143,41 @@ namespace sttsm {
 
 int* batch_status_word() { return status_dev(); }
 int peek_status_word() { return g_status_host ? __atomic_load_n(g_status_host, __ATOMIC_SEQ_CST) : 0; }
+
+int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, int npiece, int b, int m, int k)
+{
+    auto enc = get_encode_fn();
+    if (!enc) return STTSM_ERR_CUDA;
+    int64_t R = 1;
+    for (int a = 0; a < m - 1; ++a) R *= b;
+    const int64_t bm = R * b;
+    int64_t bq = 1;
+    for (int q = 0; q <= k; ++q, bq *= b) {
+        CUresult r;
+        if (q == 0) {
+            // K-major: {a (contiguous), rows (b apart), block x piece}
+            cuuint64_t dims[3] = {(cuuint64_t)b, (cuuint64_t)R, (cuuint64_t)(nblocks * npiece)};
+            cuuint64_t strides[2] = {(cuuint64_t)b * 2, (cuuint64_t)bm * 2};
+            cuuint32_t box[3] = {32, 128, (cuuint32_t)npiece};
+            cuuint32_t estr[3] = {1, 1, 1};
+            r = enc(&maps[0], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(pieces), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        } else {
+            // MN-major: {32 rows (contiguous), a (b^q apart), 32-row atoms, outer rows (b^(q+1) apart), block x piece}
+            cuuint64_t dims[5] = {32, (cuuint64_t)b, (cuuint64_t)(bq / 32), (cuuint64_t)(R / bq), (cuuint64_t)(nblocks * npiece)};
+            cuuint64_t strides[4] = {(cuuint64_t)bq * 2, 64, (cuuint64_t)bq * b * 2, (cuuint64_t)bm * 2};
+            cuuint32_t box[5] = {32, 32, (cuuint32_t)((bq < 128 ? bq : 128) / 32), (cuuint32_t)(bq < 128 ? 128 / bq : 1),
+                                 (cuuint32_t)npiece};
+            cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+            r = enc(&maps[q], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(pieces), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
+        if (r != CUDA_SUCCESS) return STTSM_ERR_CUDA;
+    }
+    return STTSM_OK;
+}
 
 int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp, int box_rows)
 {
@@ -324,6 +365,48 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
     void* bufs[2] = {ws + w.buf0, ws + w.buf1};
     const int sms = num_sms();
     const int np = npiece_of(prec);
+    if (w.tma) {
+        // TMA-fed kernel: split X and A once, temporaries as BF16 pieces
+        TmaInst tm;
+        memset(&tm, 0, sizeof(tm));
+        {
+            ProfScope ps(stream, 2, -1, 0.0);
+            rc = cuda_err(launch_split_x((const float*)X, ws + w.xpieces, (int)p, (int)n, w.rows, w.Kp, np, stream));
+            if (rc == STTSM_OK)
+                rc = cuda_err(launch_split_bcss((const float*)A, ws + w.apieces, s.lv[0].P_parent, s.bm, np, stream));
+        }
+        if (rc != STTSM_OK) return rc;
+        rc = make_x_tensor_map(&tm.tmX, ws + w.xpieces, np, w.rows, w.Kp, TC_BN);
+        if (rc != STTSM_OK) return rc;
+        for (int d = 0; d < m; ++d) {
+            const LevelShape& LS = s.lv[d];
+            const void* parent = d == 0 ? (const void*)(ws + w.apieces) : bufs[(d - 1) & 1];
+            rc = make_a_tensor_maps(tm.tmA, parent, LS.nodes_parent * LS.P_parent, np, b, m, LS.k);
+            if (rc != STTSM_OK) return rc;
+            LevelInst& L = tm.L;
+            L.parent = parent;
+            L.out = d == m - 1 ? C : bufs[d & 1];
+            L.out_np = d == m - 1 ? 0 : np;
+            L.G = P->d_G[d];
+            L.OFF = P->d_G[d] + level_G_size(s, d);
+            L.X = X;
+            L.m = m; L.b = b; L.k = LS.k; L.nbar = (int32_t)s.nbar;
+            L.n = (int32_t)n; L.p = (int32_t)p;
+            L.R = (int32_t)s.R;
+            L.Ktot = (int32_t)(s.nbar * b);
+            L.bm = s.bm;
+            L.P_parent = LS.P_parent;
+            L.P_out = LS.P_out;
+            L.rows_per_parent = LS.P_out * s.R;
+            int64_t bp = 1;
+            for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
+            const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
+            ProfScope ps(stream, 1, d, lflops);
+            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
+            if (rc != STTSM_OK) return rc;
+        }
+        return STTSM_OK;
+    }
     TcInst ti;
     memset(&ti, 0, sizeof(ti));
     if (!fp64) {

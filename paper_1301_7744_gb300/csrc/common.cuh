@@ -78,6 +78,7 @@ struct LevelInst {
     int64_t P_out;          // stored blocks per child node
     int64_t rows_per_parent;  // P_out * R
     int32_t bpow[STTSM_MAX_M + 1];
+    int32_t out_np;         // 0: FP32 output; else BF16 pieces per block [node][block][piece][b^m]
 };
 
 // Rows of a tile are mapped to (prefix block pr, row rr) by

@@ -1,0 +1,349 @@
+// kernels_tma.cu — the split-precision level kernel with the A operand loaded by
+// TMA from BF16 pieces (block sizes b that are multiples of 32 and whose output
+// blocks hold a multiple of 128 rows).
+//
+// The operands are those of level_tc_kernel (kernels_tc.cu): rows of stored
+// parent blocks gathered through G times X.  Here the parent temporaries (and A,
+// pre-split once) are stored as BF16 pieces, [node][block][piece][b^m], so every
+// 32-wide contraction stage of a 128-row tile is one box of one stored block:
+//   * insertion position q = 0: the contraction index is the block's fastest
+//     mode, rows are b apart -> a 3-D K-major box {32, 128, NP};
+//   * q >= 1: rows are contiguous in runs of b^q >= 32 and the contraction index
+//     is b^q apart -> a 5-D MN-major box {32 rows, 32 k, atoms, outer, NP} in
+//     32-row (64-byte) swizzle atoms,
+// which is how the permutation of App. A (permute before dgemm) becomes a choice
+// of tensor map and operand major-ness per stage instead of a data movement.
+//
+// CTA = 18 warps, one per SM, persistent over the tile list:
+//   warps 0-15  epilogue: D0 partials (x0*y0, restarted every 64 contraction
+//               indices) folded into FP32 registers, D1 (cross products) added at
+//               the end of the tile; the row is written as BF16 pieces for the
+//               next level (or FP32 into C at the last level);
+//   warp 16     TMEM allocation and the MMA-issuing thread;
+//   warp 17     the TMA-issuing thread (A box per stage by q, X pieces box).
+#include <cuda_bf16.h>
+#include <cuda.h>
+#include <mutex>
+#include "common.cuh"
+#include "launch.h"
+#include "tc_ptx.cuh"
+
+namespace sttsm {
+
+using namespace ptx;
+
+namespace {
+
+constexpr int T_THREADS = 576;
+constexpr int T_EPI_WARPS = 16;
+constexpr int T_MMA_WARP = 16;
+constexpr int T_TMA_WARP = 17;
+constexpr int T_GS = 2;
+
+template <int NP>
+struct SmemT {
+    static constexpr int A_PLANE = TC_BM * TC_KC * 2;
+    static constexpr int B_PLANE = TC_BN * TC_KC * 2;
+    static constexpr int STAGE = NP * (A_PLANE + B_PLANE);
+    static constexpr int STAGES = NP == 3 ? 3 : 4;
+    static constexpr int BYTES = STAGES * STAGE + 1024 + 256;
+};
+
+}  // namespace
+
+template <int NP>
+__global__ void __launch_bounds__(T_THREADS, 1)
+level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restrict__ insts,
+                 const Tile* __restrict__ tiles, int ntiles, int* status)
+{
+    using S = SmemT<NP>;
+    constexpr int STAGES = S::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = (uint64_t*)(smem + STAGES * S::STAGE);
+    uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 4);
+    volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    const uint32_t d0_full = bar0 + 8u * (2 * STAGES);
+    const uint32_t d0_empty = bar0 + 8u * (2 * STAGES + 1);
+    const uint32_t d1_empty = bar0 + 8u * (2 * STAGES + 2);
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 3);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
+        mbar_init(d0_full, 1);
+        mbar_init(d0_empty, T_EPI_WARPS);
+        mbar_init(d1_empty, T_EPI_WARPS);
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == T_MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(smem_u32(tmem_holder)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+    const uint32_t tmem_d1 = tmem_base;
+    const uint32_t tmem_d0 = tmem_base + (uint32_t)TC_BN;
+
+    if (warp == T_TMA_WARP) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_stage = -1;
+            uint32_t last_phase = 0;
+            bool ok = true;
+            for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+                const Tile t = tiles[ti];
+                const TmaInst& TI = insts ? insts[t.inst] : inst0;
+                const LevelInst& I = TI.L;
+                const int pr = t.row0 / I.R, rr0 = t.row0 - pr * I.R;
+                const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
+                const int nk = I.Ktot / TC_KC;
+                for (int ks = 0; ks < nk; ++ks) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                    const int k0 = ks * TC_KC, ib = k0 / I.b, a0 = k0 - ib * I.b;
+                    const int32_t gq = __ldg(Grow + ib);
+                    const int q = gq & 7;
+                    const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
+                    const uint32_t sA = smem_u32(smem + stage * S::STAGE);
+                    const uint32_t sB = sA + NP * S::A_PLANE;
+                    mbar_arrive_expect_tx(full_bar(stage), (uint32_t)S::STAGE);
+                    if (q == 0) {
+                        tma_load_3d(sA, &TI.tmA[0], a0, rr0, bp, full_bar(stage));
+                    } else {
+                        const int bq = I.bpow[q];
+                        tma_load_5d(sA, &TI.tmA[q], 0, a0, (rr0 % bq) >> 5, rr0 / bq, bp, full_bar(stage));
+                    }
+                    tma_load_3d(sB, &TI.tmX, k0, t.col0, 0, full_bar(stage));
+                    last_stage = stage;
+                    last_phase = phase;
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                }
+            }
+            if (!ok && last_stage >= 0) {
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(full_bar(last_stage), last_phase))
+                    if (globaltimer() - t0 > WAIT_LIMIT_NS) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp == T_MMA_WARP) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, group_phase = 0, tile_phase = 0;
+            bool ok = true, issued = false;
+            for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+                const Tile t = tiles[ti];
+                const TmaInst& TI = insts ? insts[t.inst] : inst0;
+                const LevelInst& I = TI.L;
+                const int pr = t.row0 / I.R;
+                const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
+                const int nk = I.Ktot / TC_KC;
+                const int nmma = (t.ncols + 15) & ~15;
+                const uint32_t idesc_k = idesc_bf16(nmma), idesc_mn = idesc_bf16_amn(nmma);
+                if (!mbar_wait(d1_empty, tile_phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                tile_phase ^= 1u;
+                tc_fence_after();
+                for (int ks = 0; ks < nk; ++ks) {
+                    const int ib = (ks * TC_KC) / I.b;
+                    const bool mn = (__ldg(Grow + ib) & 7) != 0;
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sA = smem_u32(smem + stage * S::STAGE);
+                    const uint32_t sB = sA + NP * S::A_PLANE;
+                    const uint32_t idesc = mn ? idesc_mn : idesc_k;
+                    auto adesc = [&](int s, int kh) {
+                        return mn ? smem_desc_sw64_mn(sA + s * S::A_PLANE + kh * 1024)
+                                  : smem_desc_sw64(sA + s * S::A_PLANE + kh * 32);
+                    };
+#pragma unroll
+                    for (int kh = 0; kh < TC_KC / 16; ++kh) {
+#pragma unroll
+                        for (int s = 0; s < NP; ++s) {
+#pragma unroll
+                            for (int u = 0; u < NP; ++u) {
+                                if (s + u > NP - 1 || s + u == 0) continue;
+                                const uint64_t bd = smem_desc_sw64(sB + u * S::B_PLANE + kh * 32);
+                                const bool first = ks == 0 && kh == 0 && s == 0 && u == 1;
+                                tc_mma(tmem_d1, adesc(s, kh), bd, idesc, first ? 0u : 1u);
+                                issued = true;
+                            }
+                        }
+                    }
+                    const bool group_start = (ks % T_GS) == 0;
+                    if (group_start) {
+                        if (!mbar_wait(d0_empty, group_phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                        group_phase ^= 1u;
+                        tc_fence_after();
+                    }
+#pragma unroll
+                    for (int kh = 0; kh < TC_KC / 16; ++kh)
+                        tc_mma(tmem_d0, adesc(0, kh), smem_desc_sw64(sB + kh * 32), idesc, (group_start && kh == 0) ? 0u : 1u);
+                    tc_commit(empty_bar(stage));
+                    if ((ks % T_GS) == T_GS - 1 || ks == nk - 1) tc_commit(d0_full);
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                }
+            }
+            if (!ok && issued) {
+                tc_commit(drain_bar);
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(drain_bar, 0))
+                    if (globaltimer() - t0 > WAIT_LIMIT_NS) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 0-15)
+        const int quad = warp & 3, cq = warp >> 2;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        const int colbase = cq * 64;
+        uint32_t group_phase = 0;
+        bool ok = true;
+        float acc[64];
+        auto fold = [&](uint32_t tm, bool active) {
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float v[8];
+                    tmem_ld_32x32b_x8(tm + lane_off + colbase + c * 8, v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
+                }
+            }
+        };
+        for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+            const Tile t = tiles[ti];
+            const TmaInst& TI = insts ? insts[t.inst] : inst0;
+            const LevelInst& I = TI.L;
+            const int nk = I.Ktot / TC_KC;
+            const int ngroups = (nk + T_GS - 1) / T_GS;
+            const bool active = colbase < t.ncols;
+#pragma unroll
+            for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+            for (int gi = 0; gi < ngroups; ++gi) {
+                if (!mbar_wait(d0_full, group_phase, abort_flag, status)) { ok = false; break; }
+                group_phase ^= 1u;
+                tc_fence_after();
+                fold(tmem_d0, active);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(d0_empty);
+            }
+            if (!ok) break;
+            fold(tmem_d1, active);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(d1_empty);
+            const int g = t.row0 + row;
+            if (active && g < I.rows_per_parent) {
+                const int pr = g / I.R, rr = g - pr * I.R;
+                const int b = I.b, bk = I.bpow[I.k];
+                const int64_t rowoff = __ldg(I.OFF + I.k * I.R + rr);
+                const int cg0 = t.col0 + colbase;
+                int jb = cg0 / b, c = cg0 - jb * b;
+                const int nvalid = t.ncols - colbase;
+                if (I.out_np == 0) {
+                    float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) {
+                        if (e < nvalid) dst[(int64_t)bk * c] = acc[e];
+                        if (++c == b) { c = 0; dst += I.P_out * I.bm; }
+                    }
+                } else {
+                    // BF16 pieces of the next level's operand: [node][block][piece][b^m]
+                    __nv_bfloat16* dst = (__nv_bfloat16*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * NP * I.bm + rowoff;
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) {
+                        if (e < nvalid) {
+                            float x = acc[e];
+#pragma unroll
+                            for (int pc = 0; pc < NP; ++pc) {
+                                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                                dst[(int64_t)pc * I.bm + (int64_t)bk * c] = h;
+                                x -= __bfloat162float(h);
+                            }
+                        }
+                        if (++c == b) { c = 0; dst += I.P_out * NP * I.bm; }
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == T_MMA_WARP) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem_base));
+    }
+}
+
+// FP32 BCSS -> NP BF16 pieces per block, [block][piece][b^m].
+template <int NP>
+__global__ void split_bcss_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, int64_t nblocks, int64_t bm)
+{
+    const int64_t total = nblocks * bm;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = i / bm, e = i - blk * bm;
+        float x = in[i];
+        __nv_bfloat16* o = out + blk * NP * bm + e;
+#pragma unroll
+        for (int pc = 0; pc < NP; ++pc) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            o[pc * bm] = h;
+            x -= __bfloat162float(h);
+        }
+    }
+}
+
+int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s)
+{
+    const int64_t total = nblocks * bm;
+    int64_t g = (total + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    if (npiece == 3) split_bcss_kernel<3><<<(int)g, 256, 0, s>>>(in, (__nv_bfloat16*)out, nblocks, bm);
+    else if (npiece == 2) split_bcss_kernel<2><<<(int)g, 256, 0, s>>>(in, (__nv_bfloat16*)out, nblocks, bm);
+    else return (int)cudaErrorInvalidValue;
+    return (int)cudaGetLastError();
+}
+
+int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
+                     int num_sms, int* d_status, cudaStream_t s)
+{
+    if (ntiles <= 0) return 0;
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    static std::mutex mu;
+    static bool attr_set[2][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 0 && dev < 64 && !attr_set[npiece - 2][dev]) {
+            cudaError_t e = npiece == 3
+                ? cudaFuncSetAttribute(level_tma_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<3>::BYTES)
+                : cudaFuncSetAttribute(level_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<2>::BYTES);
+            if (e != cudaSuccess) return (int)e;
+            attr_set[npiece - 2][dev] = true;
+        }
+    }
+    if (npiece == 3)
+        level_tma_kernel<3><<<grid, T_THREADS, SmemT<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
+    else
+        level_tma_kernel<2><<<grid, T_THREADS, SmemT<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace sttsm

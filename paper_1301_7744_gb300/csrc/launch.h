@@ -45,6 +45,21 @@ constexpr int TC_SMALL_BN = 64;
 int launch_level_tc_small(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
                           int num_sms, int* d_status, cudaStream_t s);
 
+// TMA-fed variant (kernels_tma.cu): parent temporaries (and A) as BF16 pieces
+// [node][block][piece][b^m]; tmA[q] maps the parent for insertion position q.
+struct TmaInst {
+    CUtensorMap tmX;
+    CUtensorMap tmA[STTSM_MAX_M];
+    LevelInst L;
+};
+int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
+                     int num_sms, int* d_status, cudaStream_t s);
+int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s);
+
+// Tensor maps of a BF16-piece parent array with nblocks stored blocks (all
+// nodes) for insertion positions q = 0..k of a level (see kernels_tma.cu).
+int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, int npiece, int b, int m, int k);
+
 // Builds the TMA descriptor of an X-piece array (box: TC_KC x box_rows x npiece).
 int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp, int box_rows = TC_BN);
 
