@@ -376,7 +376,8 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
                 rc = cuda_err(launch_split_bcss((const float*)A, ws + w.apieces, s.lv[0].P_parent, s.bm, np, stream));
         }
         if (rc != STTSM_OK) return rc;
-        rc = make_x_tensor_map(&tm.tmX, ws + w.xpieces, np, w.rows, w.Kp, TC_BN);
+        for (int xs = 0; xs < 3 && rc == STTSM_OK; ++xs)
+            rc = make_x_tensor_map(&tm.tmX[xs], ws + w.xpieces, np, w.rows, w.Kp, TC_BN >> xs);
         if (rc != STTSM_OK) return rc;
         for (int d = 0; d < m; ++d) {
             const LevelShape& LS = s.lv[d];
@@ -402,7 +403,7 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
             for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
             const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
             ProfScope ps(stream, 1, d, lflops);
-            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
+            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d == m - 1, stream));
             if (rc != STTSM_OK) return rc;
         }
         return STTSM_OK;

@@ -51,7 +51,7 @@ struct SmemT {
 
 }  // namespace
 
-template <int NP>
+template <int NP, bool FP32_OUT>
 __global__ void __launch_bounds__(T_THREADS, 1)
 level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restrict__ insts,
                  const Tile* __restrict__ tiles, int ntiles, int* status)
@@ -117,14 +117,16 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
                     const uint32_t sA = smem_u32(smem + stage * S::STAGE);
                     const uint32_t sB = sA + NP * S::A_PLANE;
-                    mbar_arrive_expect_tx(full_bar(stage), (uint32_t)S::STAGE);
+                    // X box rows: the smallest of 256 / 128 / 64 that covers the tile's columns
+                    const int xsel = t.ncols > 128 ? 0 : (t.ncols > 64 ? 1 : 2);
+                    mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(NP * S::A_PLANE + (NP * S::B_PLANE >> xsel)));
                     if (q == 0) {
                         tma_load_3d(sA, &TI.tmA[0], a0, rr0, bp, full_bar(stage));
                     } else {
                         const int bq = I.bpow[q];
                         tma_load_5d(sA, &TI.tmA[q], 0, a0, (rr0 % bq) >> 5, rr0 / bq, bp, full_bar(stage));
                     }
-                    tma_load_3d(sB, &TI.tmX, k0, t.col0, 0, full_bar(stage));
+                    tma_load_3d(sB, &TI.tmX[xsel], k0, t.col0, 0, full_bar(stage));
                     last_stage = stage;
                     last_phase = phase;
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -152,6 +154,9 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int nk = I.Ktot / TC_KC;
                 const int nmma = (t.ncols + 15) & ~15;
                 const uint32_t idesc_k = idesc_bf16(nmma), idesc_mn = idesc_bf16_amn(nmma);
+                // B piece planes are as tall as the X box the producer used
+                const int xsel = t.ncols > 128 ? 0 : (t.ncols > 64 ? 1 : 2);
+                const uint32_t b_plane = (uint32_t)(S::B_PLANE >> xsel);
                 if (!mbar_wait(d1_empty, tile_phase ^ 1u, abort_flag, status)) { ok = false; break; }
                 tile_phase ^= 1u;
                 tc_fence_after();
@@ -174,7 +179,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
 #pragma unroll
                             for (int u = 0; u < NP; ++u) {
                                 if (s + u > NP - 1 || s + u == 0) continue;
-                                const uint64_t bd = smem_desc_sw64(sB + u * S::B_PLANE + kh * 32);
+                                const uint64_t bd = smem_desc_sw64(sB + u * b_plane + kh * 32);
                                 const bool first = ks == 0 && kh == 0 && s == 0 && u == 1;
                                 tc_mma(tmem_d1, adesc(s, kh), bd, idesc, first ? 0u : 1u);
                                 issued = true;
@@ -254,12 +259,15 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int cg0 = t.col0 + colbase;
                 int jb = cg0 / b, c = cg0 - jb * b;
                 const int nvalid = t.ncols - colbase;
-                if (I.out_np == 0) {
+                if constexpr (FP32_OUT) {
                     float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
+                    // the FP32 output is C (k = 0): a row's columns are contiguous within a
+                    // child's block, and b (a multiple of 32) keeps groups of 4 inside blocks
 #pragma unroll
-                    for (int e = 0; e < 64; ++e) {
-                        if (e < nvalid) dst[(int64_t)bk * c] = acc[e];
-                        if (++c == b) { c = 0; dst += I.P_out * I.bm; }
+                    for (int e = 0; e < 64; e += 4) {
+                        if (e < nvalid) *(float4*)(dst + c) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                        c += 4;
+                        if (c == b) { c = 0; dst += I.P_out * I.bm; }
                     }
                 } else {
                     // BF16 pieces of the next level's operand: [node][block][piece][b^m]
@@ -320,29 +328,36 @@ int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, i
 }
 
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, cudaStream_t s)
+                     int num_sms, int* d_status, bool fp32_out, cudaStream_t s)
 {
     if (ntiles <= 0) return 0;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
     static std::mutex mu;
-    static bool attr_set[2][64] = {};
+    static bool attr_set[4][64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
+    const int v = (npiece - 2) * 2 + (fp32_out ? 1 : 0);
     {
         std::lock_guard<std::mutex> lock(mu);
-        if (dev >= 0 && dev < 64 && !attr_set[npiece - 2][dev]) {
-            cudaError_t e = npiece == 3
-                ? cudaFuncSetAttribute(level_tma_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<3>::BYTES)
-                : cudaFuncSetAttribute(level_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<2>::BYTES);
+        if (dev >= 0 && dev < 64 && !attr_set[v][dev]) {
+            cudaError_t e;
+            switch (v) {
+            case 0: e = cudaFuncSetAttribute(level_tma_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<2>::BYTES); break;
+            case 1: e = cudaFuncSetAttribute(level_tma_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<2>::BYTES); break;
+            case 2: e = cudaFuncSetAttribute(level_tma_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<3>::BYTES); break;
+            default: e = cudaFuncSetAttribute(level_tma_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<3>::BYTES); break;
+            }
             if (e != cudaSuccess) return (int)e;
-            attr_set[npiece - 2][dev] = true;
+            attr_set[v][dev] = true;
         }
     }
-    if (npiece == 3)
-        level_tma_kernel<3><<<grid, T_THREADS, SmemT<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
-    else
-        level_tma_kernel<2><<<grid, T_THREADS, SmemT<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
+    switch (v) {
+    case 0: level_tma_kernel<2, false><<<grid, T_THREADS, SmemT<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status); break;
+    case 1: level_tma_kernel<2, true><<<grid, T_THREADS, SmemT<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status); break;
+    case 2: level_tma_kernel<3, false><<<grid, T_THREADS, SmemT<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status); break;
+    default: level_tma_kernel<3, true><<<grid, T_THREADS, SmemT<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status); break;
+    }
     return (int)cudaGetLastError();
 }
 

@@ -48,12 +48,13 @@ int launch_level_tc_small(int npiece, const TcInst& inst0, const TcInst* d_insts
 // TMA-fed variant (kernels_tma.cu): parent temporaries (and A) as BF16 pieces
 // [node][block][piece][b^m]; tmA[q] maps the parent for insertion position q.
 struct TmaInst {
-    CUtensorMap tmX;
+    CUtensorMap tmX[3];            // X pieces with box rows 256, 128, 64 (chosen per tile by its columns)
     CUtensorMap tmA[STTSM_MAX_M];
     LevelInst L;
 };
+// fp32_out: the launch writes FP32 (C at the last level) instead of BF16 pieces.
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, cudaStream_t s);
+                     int num_sms, int* d_status, bool fp32_out, cudaStream_t s);
 int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s);
 
 // Tensor maps of a BF16-piece parent array with nblocks stored blocks (all
