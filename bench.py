@@ -257,6 +257,21 @@ def time_steps(torch, fn, steps, warmup, per_step_events=True):
     return t_all0.elapsed_time(t_all1), per
 
 
+def profiled_traffic(b, prec, kinds):
+    """DRAM bytes (read + write) per step of the level kernel, summed over the m level
+    launches, from the committed ncu summary of this workload (profiles/traffic.json),
+    or None when no capture of the current kernel for this block size exists."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    key = "%s_b%d_%s" % (kinds[0] if kinds else "", b, prec)
+    v = d.get(key)
+    return v.get("dram_bytes_per_step") if isinstance(v, dict) else None
+
+
 def end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, steps):
     """Same metric through sttsm_bcss_host: H2D of A and X from pinned host
     buffers, the computation, D2H of C, all inside the timed region."""
@@ -606,7 +621,8 @@ def main():
 
     # ---- dominant kernel roofline from the library's per-launch events
     recs = st.sttsm_profile_read()
-    tc = [r for r in recs if r["kind"] == "tc"]
+    tc = [r for r in recs if r["kind"] in ("tc", "tma")]
+    kinds = sorted({r["kind"] for r in tc})
     kern_ms = sum(r["ms"] for r in tc)
     kern_flops = sum(r["useful_flops"] for r in tc)
     nprod = 6 if prec == st.STTSM_BF16X6 else 3
@@ -623,9 +639,10 @@ def main():
                        "useful_tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12,
                        "mma_frac_of_peak": v["flops"] * nprod / (v["ms"] * 1e-3) / 1e12 / peak}
               for k, v in sorted(per_level.items())}
+    traffic = profiled_traffic(b, args.prec, kinds)
     roofline = {"bound": "tensor", "achieved": mma_tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": mma_tflops / peak, "traffic": None,
-                "kernel": "level_tc_kernel<3> (all levels)",
+                "frac": mma_tflops / peak, "traffic": traffic,
+                "kernel": {"tma": "level_tma_kernel", "tc": "level_tc_kernel"}[kinds[0]] + " (all m levels)" if kinds else None,
                 "achieved_counts": "useful flops x %d piece products per launch / CUDA-event duration" % nprod,
                 "peak_source": "bf16_tflops_sustained of %s MEASURED_PEAKS" % pk_src,
                 "useful_tflops": kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else 0.0,

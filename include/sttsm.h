@@ -256,7 +256,8 @@ int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_
  * every kernel sttsm_bcss launches is bracketed by CUDA events on its
  * stream.  sttsm_profile_enable(1) clears earlier records; (0) stops.
  * sttsm_profile_read waits for the recorded events and copies up to `max`
- * records: kind (0 = FP64 level, 1 = tensor-core level, 2 = X split),
+ * records: kind (0 = FP64 level, 1 = tensor-core level with gathered A,
+ * 2 = operand split, 3 = tensor-core level with TMA-fed A),
  * level d, useful flops of that launch (Tbl. 4 terms of level d; 0 for the
  * split), and its duration in ms.  *count receives the number of records. */
 int sttsm_profile_enable(int on);

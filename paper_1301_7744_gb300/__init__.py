@@ -387,7 +387,7 @@ def sttsm_profile_enable(on: bool) -> None:
 
 
 def sttsm_profile_read() -> list[dict]:
-    """Recorded launches: dicts with kind ('fp64' | 'tc' | 'split'), level, useful_flops, ms."""
+    """Recorded launches: dicts with kind ('fp64' | 'tc' | 'tma' | 'split'), level, useful_flops, ms."""
     import numpy as np
     L = _load()
     cnt = ctypes.c_int(0)
@@ -399,7 +399,7 @@ def sttsm_profile_read() -> list[dict]:
     ms = np.zeros(n, dtype=np.float32)
     _check("sttsm_profile_read", L.sttsm_profile_read(n, kind.ctypes.data, level.ctypes.data, flops.ctypes.data,
                                                       ms.ctypes.data, ctypes.byref(cnt)))
-    names = {0: "fp64", 1: "tc", 2: "split"}
+    names = {0: "fp64", 1: "tc", 2: "split", 3: "tma"}
     return [dict(kind=names[int(k)], level=int(l), useful_flops=float(f), ms=float(t))
             for k, l, f, t in zip(kind, level, flops, ms)]
 

@@ -316,14 +316,46 @@ __global__ void split_bcss_kernel(const float* __restrict__ in, __nv_bfloat16* _
     }
 }
 
+// The same with 8 entries per thread: two 16-byte loads, one 16-byte store per piece.
+template <int NP>
+__global__ void split_bcss_vec8_kernel(const float4* __restrict__ in, uint4* __restrict__ out, int64_t nblocks, int64_t bm8)
+{
+    const int64_t total = nblocks * bm8;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = i / bm8, e = i - blk * bm8;
+        const float4 x0 = in[2 * i], x1 = in[2 * i + 1];
+        float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+        for (int pc = 0; pc < NP; ++pc) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const __nv_bfloat16 b0 = __float2bfloat16_rn(v[2 * h]), b1 = __float2bfloat16_rn(v[2 * h + 1]);
+                w[h] = pack_bf16x2(b0, b1);
+                v[2 * h] -= __bfloat162float(b0);
+                v[2 * h + 1] -= __bfloat162float(b1);
+            }
+            out[(blk * NP + pc) * bm8 + e] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
 int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s)
 {
+    if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
+    if (bm % 8 == 0 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
+        const int64_t total = nblocks * (bm / 8);
+        int64_t g = (total + 255) / 256;
+        if (g > 152 * 32) g = 152 * 32;
+        if (npiece == 3) split_bcss_vec8_kernel<3><<<(int)g, 256, 0, s>>>((const float4*)in, (uint4*)out, nblocks, bm / 8);
+        else split_bcss_vec8_kernel<2><<<(int)g, 256, 0, s>>>((const float4*)in, (uint4*)out, nblocks, bm / 8);
+        return (int)cudaGetLastError();
+    }
     const int64_t total = nblocks * bm;
     int64_t g = (total + 255) / 256;
     if (g > 152 * 32) g = 152 * 32;
     if (npiece == 3) split_bcss_kernel<3><<<(int)g, 256, 0, s>>>(in, (__nv_bfloat16*)out, nblocks, bm);
-    else if (npiece == 2) split_bcss_kernel<2><<<(int)g, 256, 0, s>>>(in, (__nv_bfloat16*)out, nblocks, bm);
-    else return (int)cudaErrorInvalidValue;
+    else split_bcss_kernel<2><<<(int)g, 256, 0, s>>>(in, (__nv_bfloat16*)out, nblocks, bm);
     return (int)cudaGetLastError();
 }
 
