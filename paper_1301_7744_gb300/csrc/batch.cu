@@ -28,27 +28,39 @@ inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int npiece(int prec) { return prec == STTSM_BF16X6 ? 3 : (prec == STTSM_BF16X3 ? 2 : 0); }
 
-// Cost model of one level launch's tiles, in tensor-core cycles on one SM:
-// each stage of a tile costs the larger of its MMA time (products x 2 K-steps
-// x N/2 cycles for a 128 x N x 16 MMA) and the gather latency of a stage; a
-// tile adds a fixed cost for its set-up, flushes and stores.
-double tile_cost(int nk, int ncols, int nprod)
+// Cost model of one level launch's tiles, in SM cycles: each stage of a tile
+// costs the larger of its MMA time (products x 2 K-steps x N/2 cycles for a
+// 128 x N x 16 MMA) and the stage's operand-supply floor, and each tile adds a
+// fixed cost (set-up, flushes, stores).  The floors and tile costs differ by
+// kernel: TMA-fed (operands by TMA, no gather), gathered (per-stage gather
+// latency), small-tile (two CTAs per SM, latency-bound tiles).
+struct KernelCost { double stage_floor, tile; };
+
+KernelCost kernel_cost(const Shape& s)
+{
+    if (tc_small_mode(s)) return {700.0, 4000.0};
+    if (tc_tma_mode(s)) return {300.0, 3000.0};
+    return {1100.0, 3000.0};
+}
+
+double tile_cost(int nk, int ncols, int nprod, const KernelCost& k)
 {
     const double n16 = (double)((ncols + 15) & ~15);
     const double mma = nprod * 2.0 * n16 / 2.0;
-    return nk * std::max(mma, 900.0) + 2500.0;
+    return nk * std::max(mma, k.stage_floor) + k.tile;
 }
 
 double plan_cost(const Shape& s, int prec, int BM, int BN)
 {
     const int nprod = prec == STTSM_BF16X3 ? 3 : 6;
     if (tc_small_mode(s)) BN = TC_SMALL_BN;
+    const KernelCost k = kernel_cost(s);
     double c = 0.0;
     for (int d = 0; d < s.m; ++d) {
         std::vector<Tile> tiles;
         build_level_tiles(s, d, BM, BN, 0, tiles);
         const int nk = (int)((s.nbar * s.b + TC_KC - 1) / TC_KC);
-        for (const Tile& t : tiles) c += tile_cost(nk, t.ncols, nprod);
+        for (const Tile& t : tiles) c += tile_cost(nk, t.ncols, nprod, k);
     }
     return c;
 }

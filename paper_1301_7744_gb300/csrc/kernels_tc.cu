@@ -402,15 +402,19 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
 // ---------------------------------------------------------------------------
 // Small-tile variant for launches whose contraction is short (n̄ b <= 64, at
 // most two stages: one D0 group, so no register running sum is needed) —
-// e.g. batches of small instances.  Tiles are 128 x 64; TMEM holds two tile
-// slots (D1, D0 of 64 columns each) so the MMA runs one tile ahead of the
-// epilogue; 9 warps and ~110 KB of shared memory let two CTAs share an SM.
-//   warps 0-7  workers: rows 32 (w % 4) .. +31; per stage each thread
-//              gathers the 16 contraction entries 16 (w / 4) .. +15 of its
-//              row (two SW64 chunks); the epilogue of tile t-1 runs after the
-//              production of tile t: columns 32 (w / 4) .. +31 of D0 + D1.
+// e.g. batches of small instances, where per-tile latency, not the tensor
+// core, sets the pace.  Tiles are 128 x 64; TMEM holds two tile slots (D1,
+// D0 of 64 columns each) so the MMA runs one tile ahead of the epilogue;
+// 10 warps and ~110 KB of shared memory let two CTAs share an SM.
+//   warps 0-7  workers: rows 32 (w % 4) .. +31; per stage each thread stores
+//              the 16 contraction entries 16 (w / 4) .. +15 of its row (two
+//              SW64 chunks) from a ring of three gathered stages held in
+//              registers, then gathers the stage three ahead into the freed
+//              slot; the epilogue of tile t-1 runs after the production of
+//              tile t: columns 32 (w / 4) .. +31 of D0 + D1.
 //   warp 8     TMEM allocation and the MMA-issuing thread.
-constexpr int SM_THREADS = 288;
+//   warp 9     the X-box TMA thread, issuing each stage as soon as it frees.
+constexpr int SM_THREADS = 320;
 constexpr int SM_BN = 64;
 
 template <int NP>
@@ -420,6 +424,11 @@ struct SmemSmall {
     static constexpr int STAGE = NP * (A_PLANE + B_PLANE);
     static constexpr int STAGES = 3;
     static constexpr int BYTES = STAGES * STAGE + 1024 + 256;
+};
+
+// Work-item cursor of the small kernel: (tile, stage) in this CTA's share.
+struct ItemCursor {
+    int ti, ks, nk;
 };
 
 template <int NP>
@@ -462,19 +471,28 @@ level_tc_small_kernel(const __grid_constant__ TcInst inst0, const TcInst* __rest
     const uint32_t tmem_base = *tmem_holder;
     // slot a: D1 at columns 128 a .. +63, D0 at 128 a + 64 .. +63
 
+    auto nk_of = [&](int ti) {
+        const Tile t = tiles[ti];
+        return ((insts ? insts[t.inst] : inst0).L.Ktot + TC_KC - 1) / TC_KC;
+    };
+    auto advance = [&](ItemCursor& c) {
+        if (++c.ks == c.nk) {
+            c.ti += gridDim.x;
+            c.ks = 0;
+            if (c.ti < ntiles) c.nk = nk_of(c.ti);
+        }
+    };
+
     if (warp < 8) {
         // ------------------------------------------------------------ workers
         const int quad = warp & 3, half = warp >> 2;
         const int row = quad * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
         const int colbase = half * 32;
-        const bool tma_thread = threadIdx.x == 0;
         int stage = 0;
         uint32_t phase = 0, accf_phase = 0;
-        int last_stage_issued = -1;
-        uint32_t last_phase_issued = 0;
         bool ok = true;
-        float va[8], vb[8];
+        float ring[3][16];
 
         // epilogue of the tile pti (slot pit & 1): D0 + D1 -> the children's blocks
         auto finish = [&](int pti, int pit) -> bool {
@@ -484,99 +502,109 @@ level_tc_small_kernel(const __grid_constant__ TcInst inst0, const TcInst* __rest
             tc_fence_after();
             const Tile t = tiles[pti];
             const LevelInst& I = (insts ? insts[t.inst] : inst0).L;
-            const bool active = colbase < t.ncols;
-            float out_v[32];
-            if (active) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
+            // 8 columns at a time: TMEM loads, sum, stores (keeps few registers live)
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                if (colbase + c * 8 < t.ncols) {      // warp-uniform
                     float d0[8], d1[8];
                     tmem_ld_32x32b_x8(tmem_base + lane_off + slot * 128 + 64 + colbase + c * 8, d0);
                     tmem_ld_32x32b_x8(tmem_base + lane_off + slot * 128 + colbase + c * 8, d1);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) out_v[c * 8 + i] = d0[i] + d1[i];
+                    for (int i = 0; i < 8; ++i) d0[i] += d1[i];
+                    store_row<8>(t, I, row, colbase + c * 8, d0);
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar(slot));
-            if (active) store_row<32>(t, I, row, colbase, out_v);
             return true;
         };
+        // gather the item of cursor g into ring slot r
+        auto gather_item = [&](const ItemCursor& g, float* dst) {
+            const Tile t = tiles[g.ti];
+            const LevelInst& I = (insts ? insts[t.inst] : inst0).L;
+            const GatherRow GR = gather_row(t, I, row);
+            gather8(GR, I, g.ks * TC_KC + half * 16, dst);
+            gather8(GR, I, g.ks * TC_KC + half * 16 + 8, dst + 8);
+        };
 
-        // work items are (tile, stage); the gather of the next item is issued
-        // right after the current one is stored (one call site)
-        int ti = blockIdx.x, ks = 0, it = 0;
-        int prev_ti = -1;
-        Tile t = ti < ntiles ? tiles[ti] : Tile{};
-        const TcInst* TIp = ti < ntiles ? (insts ? insts + t.inst : &inst0) : &inst0;
-        GatherRow GR = gather_row(t, TIp->L, row);
-        int nk = (TIp->L.Ktot + TC_KC - 1) / TC_KC;
-        if (ti < ntiles) {
-            gather8(GR, TIp->L, half * 16, va);
-            gather8(GR, TIp->L, half * 16 + 8, vb);
-        }
-        while (ti < ntiles) {
-            if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
-            uint8_t* sA = smem + stage * S::STAGE;
-            uint8_t* sB = sA + NP * S::A_PLANE;
-            if (tma_thread) {
-                mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(NP * S::B_PLANE));
-                tma_load_3d(smem_u32(sB), &TIp->tmX, ks * TC_KC, t.col0, 0, full_bar(stage));
-                last_stage_issued = stage;
-                last_phase_issued = phase;
-            }
+        ItemCursor cc{(int)blockIdx.x, 0, 0}, gc{(int)blockIdx.x, 0, 0};
+        if (cc.ti < ntiles) cc.nk = gc.nk = nk_of(cc.ti);
 #pragma unroll
-            for (int hc = 0; hc < 2; ++hc) {
-                float* v = hc ? vb : va;
-                const int cq = half * 2 + hc;
-                const uint32_t addr0 = smem_u32(sA) + row * 64 + ((cq ^ ((row >> 1) & 3)) << 4);
+        for (int r = 0; r < 3; ++r)
+            if (gc.ti < ntiles) { gather_item(gc, ring[r]); advance(gc); }
+        int prev_ti = -1, it = 0;
+        while (cc.ti < ntiles && ok) {
 #pragma unroll
-                for (int pc = 0; pc < NP; ++pc) {
-                    uint32_t w[4];
+            for (int r = 0; r < 3; ++r) {
+                if (cc.ti >= ntiles || !ok) break;
+                if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                const uint32_t sA = smem_u32(smem + stage * S::STAGE);
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const __nv_bfloat16 b0 = __float2bfloat16_rn(v[2 * h]), b1 = __float2bfloat16_rn(v[2 * h + 1]);
-                        w[h] = pack_bf16x2(b0, b1);
-                        v[2 * h] -= __bfloat162float(b0);
-                        v[2 * h + 1] -= __bfloat162float(b1);
+                for (int hc = 0; hc < 2; ++hc) {
+                    float* v = ring[r] + hc * 8;
+                    const int cq = half * 2 + hc;
+                    const uint32_t addr0 = sA + row * 64 + ((cq ^ ((row >> 1) & 3)) << 4);
+#pragma unroll
+                    for (int pc = 0; pc < NP; ++pc) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const __nv_bfloat16 b0 = __float2bfloat16_rn(v[2 * h]), b1 = __float2bfloat16_rn(v[2 * h + 1]);
+                            w[h] = pack_bf16x2(b0, b1);
+                            v[2 * h] -= __bfloat162float(b0);
+                            v[2 * h + 1] -= __bfloat162float(b1);
+                        }
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                                     :: "r"(addr0 + pc * S::A_PLANE), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
                     }
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                                 :: "r"(addr0 + pc * S::A_PLANE), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
                 }
-            }
-            fence_proxy_async();
-            mbar_arrive(full_bar(stage));
-            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-            // advance to the next item and issue its gather
-            const int cur_ti = ti;
-            const bool tile_done = ++ks == nk;
-            if (tile_done) {
-                ti += gridDim.x;
-                ks = 0;
-                if (ti < ntiles) {
-                    t = tiles[ti];
-                    TIp = insts ? insts + t.inst : &inst0;
-                    GR = gather_row(t, TIp->L, row);
-                    nk = (TIp->L.Ktot + TC_KC - 1) / TC_KC;
+                fence_proxy_async();
+                mbar_arrive(full_bar(stage));
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                // refill this ring slot with the item three ahead
+                if (gc.ti < ntiles) { gather_item(gc, ring[r]); advance(gc); }
+                const int cur_ti = cc.ti;
+                const bool tile_done = cc.ks + 1 == cc.nk;
+                advance(cc);
+                if (tile_done) {
+                    // the previous tile's epilogue overlaps this tile's MMAs
+                    if (prev_ti >= 0 && !finish(prev_ti, it - 1)) { ok = false; break; }
+                    prev_ti = cur_ti;
+                    ++it;
                 }
-            }
-            if (ti < ntiles) {
-                gather8(GR, TIp->L, ks * TC_KC + half * 16, va);
-                gather8(GR, TIp->L, ks * TC_KC + half * 16 + 8, vb);
-            }
-            if (tile_done) {
-                // the previous tile's epilogue overlaps this tile's MMAs
-                if (prev_ti >= 0 && !finish(prev_ti, it - 1)) { ok = false; break; }
-                prev_ti = cur_ti;
-                ++it;
             }
         }
         if (ok && prev_ti >= 0) ok = finish(prev_ti, it - 1);
-        if (tma_thread && !ok && last_stage_issued >= 0) {
-            uint64_t t0 = globaltimer();
-            while (!mbar_try_wait(full_bar(last_stage_issued), last_phase_issued))
-                if (globaltimer() - t0 > WAIT_LIMIT_NS) break;
+    } else if (warp == 9) {
+        // ------------------------------------------------------------ X-box producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_stage = -1;
+            uint32_t last_phase = 0;
+            bool ok = true;
+            ItemCursor c{(int)blockIdx.x, 0, 0};
+            if (c.ti < ntiles) c.nk = nk_of(c.ti);
+            while (c.ti < ntiles) {
+                if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                const Tile t = tiles[c.ti];
+                const TcInst& TI = insts ? insts[t.inst] : inst0;
+                const uint32_t sB = smem_u32(smem + stage * S::STAGE) + NP * S::A_PLANE;
+                mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(NP * S::B_PLANE));
+                tma_load_3d(sB, &TI.tmX, c.ks * TC_KC, t.col0, 0, full_bar(stage));
+                last_stage = stage;
+                last_phase = phase;
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                advance(c);
+            }
+            if (!ok && last_stage >= 0) {
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(full_bar(last_stage), last_phase))
+                    if (globaltimer() - t0 > WAIT_LIMIT_NS) break;
+            }
         }
+        __syncwarp();
     } else if (warp == 8) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
@@ -622,7 +650,7 @@ level_tc_small_kernel(const __grid_constant__ TcInst inst0, const TcInst* __rest
             }
             if (!ok && issued) {
                 tc_commit(drain_bar);
-                uint64_t t0 = globaltimer();
+                const uint64_t t0 = globaltimer();
                 while (!mbar_try_wait(drain_bar, 0))
                     if (globaltimer() - t0 > WAIT_LIMIT_NS) break;
             }

@@ -92,6 +92,8 @@ struct Req {
     sttsm_desc d;
     Shape s;
     bool small = false;
+    bool tma = false;           // TMA-fed kernel: A split once into pieces, temporaries as pieces
+    size_t a_off = 0;
     int state = Q_QUEUED;
     int level = 0;              // next level to launch
     bool split_done = false;
@@ -99,7 +101,8 @@ struct Req {
     int rows = 0, Kp = 0;
     double t_submit = 0, t_done = 0;
     std::vector<Tile> tiles[STTSM_MAX_M];
-    TcInst inst[STTSM_MAX_M];
+    std::vector<TcInst> inst;       // per level (released when the request is done)
+    std::vector<TmaInst> tinst;     // per level, TMA-fed requests only
 };
 
 struct StepRec {
@@ -163,9 +166,17 @@ int admit(sttsm_serve_s* H, Req& R)
 {
     const Shape& s = R.s;
     char* base = H->arena_base + R.ws_off;
-    CUtensorMap map;
+    CUtensorMap map, xmaps[3];
     const int box = R.small ? TC_SMALL_BN : TC_BN;
-    if (make_x_tensor_map(&map, base + R.x_off, H->np, R.rows, R.Kp, box) != STTSM_OK) return STTSM_ERR_CUDA;
+    if (R.tma) {
+        for (int xs = 0; xs < 3; ++xs)
+            if (make_x_tensor_map(&xmaps[xs], base + R.x_off, H->np, R.rows, R.Kp, TC_BN >> xs) != STTSM_OK)
+                return STTSM_ERR_CUDA;
+    } else if (make_x_tensor_map(&map, base + R.x_off, H->np, R.rows, R.Kp, box) != STTSM_OK) {
+        return STTSM_ERR_CUDA;
+    }
+    R.inst.assign(s.m, TcInst());
+    if (R.tma) R.tinst.assign(s.m, TmaInst());
     for (int d = 0; d < s.m; ++d) {
         build_level_tiles(s, d, TC_BM, box, 0, R.tiles[d]);
         const int32_t* G = nullptr;
@@ -176,8 +187,9 @@ int admit(sttsm_serve_s* H, Req& R)
         memset(&T, 0, sizeof(T));
         T.tmX = map;
         LevelInst& L = T.L;
-        L.parent = d == 0 ? R.d.A : (const void*)(base + R.buf_off[(d - 1) & 1]);
+        L.parent = d == 0 ? (R.tma ? (const void*)(base + R.a_off) : R.d.A) : (const void*)(base + R.buf_off[(d - 1) & 1]);
         L.out = d == s.m - 1 ? R.d.C : (void*)(base + R.buf_off[d & 1]);
+        L.out_np = (R.tma && d < s.m - 1) ? H->np : 0;
         L.G = G;
         L.OFF = G + level_G_size(s, d);
         L.X = R.d.X;
@@ -191,6 +203,14 @@ int admit(sttsm_serve_s* H, Req& R)
         L.rows_per_parent = LS.P_out * s.R;
         int64_t bp = 1;
         for (int q = 0; q <= STTSM_MAX_M; ++q) { L.bpow[q] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= s.b; }
+        if (R.tma) {
+            TmaInst& M = R.tinst[d];
+            memset(&M, 0, sizeof(M));
+            for (int xs = 0; xs < 3; ++xs) M.tmX[xs] = xmaps[xs];
+            if (make_a_tensor_maps(M.tmA, L.parent, LS.nodes_parent * LS.P_parent, H->np, s.b, s.m, LS.k) != STTSM_OK)
+                return STTSM_ERR_CUDA;
+            M.L = L;
+        }
     }
     return STTSM_OK;
 }
@@ -215,8 +235,11 @@ int launch_step(sttsm_serve_s* H)
 {
     std::vector<SplitDesc> split;
     int64_t split_blocks = 0;
+    std::vector<const Req*> asplit;            // TMA requests whose A is split this step
+    // groups: 0 gathered A, 1 small tiles, 2 TMA writing pieces, 3 TMA writing C
     std::vector<TcInst> insts[2];
-    std::vector<Tile> tiles[2];
+    std::vector<TmaInst> tinsts[2];
+    std::vector<Tile> tiles[4];
     std::vector<uint64_t> finishing;
     for (uint64_t tk : H->active) {
         Req& R = H->reqs[tk];
@@ -228,20 +251,24 @@ int launch_step(sttsm_serve_s* H)
             sd.first_block = split_blocks;
             split_blocks += ((int64_t)R.rows * R.Kp + 255) / 256;
             split.push_back(sd);
+            if (R.tma) asplit.push_back(&R);
             R.split_done = true;
         }
-        const int mode = R.small ? 1 : 0;
-        const int32_t e = (int32_t)insts[mode].size();
-        insts[mode].push_back(R.inst[R.level]);
+        const bool last = R.level == R.s.m - 1;
+        const int g = R.tma ? (last ? 3 : 2) : (R.small ? 1 : 0);
+        int32_t e;
+        if (g < 2) { e = (int32_t)insts[g].size(); insts[g].push_back(R.inst[R.level]); }
+        else { e = (int32_t)tinsts[g - 2].size(); tinsts[g - 2].push_back(R.tinst[R.level]); }
         for (Tile t : R.tiles[R.level]) {
             t.inst = e;
-            tiles[mode].push_back(t);
+            tiles[g].push_back(t);
         }
     }
-    // staging layout: [insts 0][insts 1][tiles 0][tiles 1][split]
-    size_t off = 0, o_i[2], o_t[2], o_s;
+    // staging layout: [TmaInst 2, 3][TcInst 0, 1][tiles 0..3][split]
+    size_t off = 0, o_ti[2], o_i[2], o_t[4], o_s;
+    for (int k = 0; k < 2; ++k) { o_ti[k] = off; off = up256(off + tinsts[k].size() * sizeof(TmaInst)); }
     for (int k = 0; k < 2; ++k) { o_i[k] = off; off = up256(off + insts[k].size() * sizeof(TcInst)); }
-    for (int k = 0; k < 2; ++k) { o_t[k] = off; off = up256(off + tiles[k].size() * sizeof(Tile)); }
+    for (int k = 0; k < 4; ++k) { o_t[k] = off; off = up256(off + tiles[k].size() * sizeof(Tile)); }
     o_s = off;
     off = up256(off + split.size() * sizeof(SplitDesc));
     Staging& S = H->stg[H->cur];
@@ -250,24 +277,32 @@ int launch_step(sttsm_serve_s* H)
     if (rc != STTSM_OK) return rc;
     if (!S.copied && cudaEventCreateWithFlags(&S.copied, cudaEventDisableTiming) != cudaSuccess) return STTSM_ERR_CUDA;
     for (int k = 0; k < 2; ++k) {
+        if (!tinsts[k].empty()) memcpy(S.h + o_ti[k], tinsts[k].data(), tinsts[k].size() * sizeof(TmaInst));
         if (!insts[k].empty()) memcpy(S.h + o_i[k], insts[k].data(), insts[k].size() * sizeof(TcInst));
-        if (!tiles[k].empty()) memcpy(S.h + o_t[k], tiles[k].data(), tiles[k].size() * sizeof(Tile));
     }
+    for (int k = 0; k < 4; ++k)
+        if (!tiles[k].empty()) memcpy(S.h + o_t[k], tiles[k].data(), tiles[k].size() * sizeof(Tile));
     if (!split.empty()) memcpy(S.h + o_s, split.data(), split.size() * sizeof(SplitDesc));
     if (cudaMemcpyAsync(S.d, S.h, off, cudaMemcpyHostToDevice, H->stream) != cudaSuccess) return STTSM_ERR_CUDA;
     if (cudaEventRecord(S.copied, H->stream) != cudaSuccess) return STTSM_ERR_CUDA;
     if (!split.empty() &&
         launch_split_x_batch((const SplitDesc*)(S.d + o_s), (int)split.size(), (int)split_blocks, H->np, H->stream) != 0)
         return STTSM_ERR_CUDA;
+    for (const Req* R : asplit)
+        if (launch_split_bcss((const float*)R->d.A, H->arena_base + R->ws_off + R->a_off, R->s.lv[0].P_parent, R->s.bm,
+                              H->np, H->stream) != 0)
+            return STTSM_ERR_CUDA;
     TcInst dummy;
     memset(&dummy, 0, sizeof(dummy));
-    for (int k = 0; k < 2; ++k) {
+    static TmaInst tdummy;   // zero-initialised; unused when a descriptor table is passed
+    for (int k = 0; k < 4; ++k) {
         if (tiles[k].empty()) continue;
-        const TcInst* di = (const TcInst*)(S.d + o_i[k]);
         const Tile* dt = (const Tile*)(S.d + o_t[k]);
         const int n = (int)tiles[k].size();
-        const int lrc = k ? launch_level_tc_small(H->np, dummy, di, dt, n, H->sms, H->status, H->stream)
-                          : launch_level_tc(H->np, dummy, di, dt, n, H->sms, H->status, H->stream);
+        int lrc;
+        if (k == 0) lrc = launch_level_tc(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, H->stream);
+        else if (k == 1) lrc = launch_level_tc_small(H->np, dummy, (const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->status, H->stream);
+        else lrc = launch_level_tma(H->np, tdummy, (const TmaInst*)(S.d + o_ti[k - 2]), dt, n, H->sms, H->status, k == 3, H->stream);
         if (lrc != 0) return STTSM_ERR_CUDA;
     }
     H->cur ^= 1;
@@ -309,6 +344,8 @@ void scheduler(sttsm_serve_s* H)
                 R.t_done = t;
                 H->arena->release(R.ws_off, R.ws_bytes);
                 for (int d = 0; d < STTSM_MAX_M; ++d) std::vector<Tile>().swap(R.tiles[d]);
+                std::vector<TcInst>().swap(R.inst);
+                std::vector<TmaInst>().swap(R.tinst);
                 ++H->n_completed;
             }
             cudaEventDestroy(H->inflight.front().ev);
@@ -398,14 +435,18 @@ int sttsm_serve_submit(void* h, const sttsm_desc* d, uint64_t* ticket)
     int rc = make_shape(d->m, d->n, d->p, d->b, &R.s);
     if (rc != STTSM_OK) return rc;
     R.small = tc_small_mode(R.s);
+    R.tma = tc_tma_mode(R.s);
     R.rows = (int)(R.s.pbar * R.s.b);
     R.Kp = (int)(((R.s.nbar * R.s.b) + 7) / 8 * 8);
     R.x_off = 0;
+    const size_t esz = R.tma ? 2 * (size_t)H->np : 4;
     size_t off = up256((size_t)H->np * R.rows * R.Kp * 2);
+    R.a_off = off;
+    if (R.tma) off += up256((size_t)H->np * R.s.lv[0].P_parent * R.s.bm * 2);
     R.buf_off[0] = off;
-    off += up256((size_t)R.s.buf_elems[0] * 4);
+    off += up256((size_t)R.s.buf_elems[0] * esz);
     R.buf_off[1] = off;
-    off += up256((size_t)R.s.buf_elems[1] * 4);
+    off += up256((size_t)R.s.buf_elems[1] * esz);
     R.ws_bytes = std::max<size_t>(off, 256);
     std::lock_guard<std::mutex> lock(H->mu);
     if (H->error) return H->error;
