@@ -378,12 +378,25 @@ def run_batch(args):
     torch.cuda.synchronize()
     capture_s = time.perf_counter() - t0
     steps = max(3, min(args.steps, 20))
+    tot_tc = None
+    if not args.no_extras:
+        # the tcgen05 small-tile kernel for the same plan (for comparison)
+        st.sttsm_set_small_kernel(st.SMALL_TCGEN05)
+        plan_tc = st.BatchPlan(insts, prec, ws_budget=int(args.ws_gb * 2 ** 30))
+        tot_tc, _ = time_steps(torch, lambda: plan_tc.run(ws), 3, 2)
+        plan_tc.destroy()
+        st.sttsm_set_small_kernel(st.SMALL_F32)
     clocks = ClockSampler()
     clocks.start()
     total_ms, per = time_steps(torch, lambda: plan.run(ws), steps, max(3, args.warmup))
     clk = clocks.stop()
     ms = total_ms / steps
     value = F / (ms * 1e-3) / 1e12
+    if args.no_extras:
+        print(json.dumps({"metric": "sttsm batch TFLOP/s", "value": value, "ms_per_step": ms, "instances": len(shapes),
+                          "useful_flops_per_step": F}), flush=True)
+        plan.destroy()
+        return 0
     # accuracy on a sample of instances against the oracle
     import oracle
     rng = np.random.default_rng(0)
@@ -426,6 +439,9 @@ def run_batch(args):
                        "plan_seconds": plan_s, "graph_capture_seconds": capture_s},
             "fp64_per_instance_loop": {"value": F / (tot64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms": tot64,
                                        "speedup_of_batch": tot64 / ms},
+            "small_kernel": "fp32 cuda-core (n̄b <= 64 contractions)",
+            "tcgen05_small_tile_kernel": {"value": F / (tot_tc / 3 * 1e-3) / 1e12, "unit": "TFLOP/s",
+                                          "ms_per_step": tot_tc / 3} if tot_tc else None,
             "rel_err": {"instances_checked": len(errs), "max": max(errs), "median": float(np.median(errs)),
                         "tolerance": 1e-6},
             "clocks": clk}

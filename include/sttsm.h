@@ -234,6 +234,13 @@ int sttsm_serve_destroy(void* handle);
 int sttsm_bcss_noalloc(const void* A_bcss, const void* X, int m, int64_t n, int64_t p, int b,
                        void* C_bcss, int prec, void* stream);
 
+/* Kernel for short contractions (n̄ b <= 64) under the split precisions:
+ * 0 (default) = FP32 FMAs on the CUDA cores, one thread per output row (at
+ * least as accurate as BF16X6; tiles of <= 64 columns and <= 64 contraction
+ * indices are latency-bound on the tensor cores); 1 = the tcgen05 small-tile
+ * kernel.  Process-wide; affects later calls and later batch-plan runs. */
+int sttsm_set_small_kernel(int kind);
+
 /* Device status word: 0 = fine; otherwise the code of the last device-side
  * failure (1 = bounded wait timed out).  Reading clears it. */
 int sttsm_device_status(void);

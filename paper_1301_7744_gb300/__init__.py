@@ -105,6 +105,8 @@ def _load():
     L.sttsm_serve_stats.restype = i32
     L.sttsm_serve_destroy.argtypes = [P]
     L.sttsm_serve_destroy.restype = i32
+    L.sttsm_set_small_kernel.argtypes = [i32]
+    L.sttsm_set_small_kernel.restype = i32
     L.sttsm_bcss_noalloc.argtypes = [P, P, i32, i64, i64, i32, P, i32, P]
     L.sttsm_bcss_noalloc.restype = i32
     L.sttsm_profile_enable.argtypes = [i32]
@@ -124,7 +126,8 @@ def exported_symbols() -> list[str]:
             "sttsm_device_status", "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read",
             "sttsm_bcss_noalloc", "sttsm_autotune_b", "sttsm_batch_plan_create", "sttsm_batch_workspace_size",
             "sttsm_batch_info", "sttsm_batch_run", "sttsm_batch_plan_destroy", "sttsm_batch", "sttsm_serve_create",
-            "sttsm_serve_submit", "sttsm_serve_poll", "sttsm_serve_stats", "sttsm_serve_destroy"]
+            "sttsm_serve_submit", "sttsm_serve_poll", "sttsm_serve_stats", "sttsm_serve_destroy",
+            "sttsm_set_small_kernel"]
 
 
 def _check(fn: str, rc: int) -> None:
@@ -360,6 +363,15 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+SMALL_F32 = 0
+SMALL_TCGEN05 = 1
+
+
+def sttsm_set_small_kernel(kind: int) -> None:
+    """Kernel for contractions n̄ b <= 64 under split precisions: SMALL_F32 (default) or SMALL_TCGEN05."""
+    _check("sttsm_set_small_kernel", _load().sttsm_set_small_kernel(kind))
 
 
 def sttsm_device_status() -> int:

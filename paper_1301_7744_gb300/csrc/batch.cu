@@ -223,6 +223,7 @@ int enqueue(sttsm_batch_plan_s* P, cudaStream_t s)
             memset(&dummy, 0, sizeof(dummy));
             const TcInst* ti = (const TcInst*)L.d_insts;
             const int rc = fp64 ? launch_level_fp64(dummy.L, (const LevelInst*)L.d_insts, L.d_tiles, L.ntiles, sms, s)
+                         : (mode && small_kernel_kind() == 0) ? launch_level_small_f32_tc(ti, L.d_tiles, L.ntiles, sms, s)
                          : mode ? launch_level_tc_small(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, s)
                                 : launch_level_tc(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, s);
             if (rc != 0) return STTSM_ERR_CUDA;

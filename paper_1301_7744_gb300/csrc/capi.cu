@@ -1,5 +1,6 @@
 // capi.cu — C ABI of the sttsm library (declared in include/sttsm.h).
 #include <cudaTypedefs.h>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -141,6 +142,9 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn()
 
 namespace sttsm {
 
+std::atomic<int> g_small_kind{0};
+int small_kernel_kind() { return g_small_kind.load(); }
+
 int* batch_status_word() { return status_dev(); }
 int peek_status_word() { return g_status_host ? __atomic_load_n(g_status_host, __ATOMIC_SEQ_CST) : 0; }
 
@@ -280,6 +284,13 @@ int sttsm_workspace_size(int m, int64_t n, int64_t p, int b, int prec, size_t* b
 }
 
 int sttsm_device_status(void) { return take_status(); }
+
+int sttsm_set_small_kernel(int kind)
+{
+    if (kind != 0 && kind != 1) return STTSM_ERR_ARG;
+    g_small_kind.store(kind);
+    return STTSM_OK;
+}
 
 int sttsm_profile_enable(int on)
 {
@@ -440,6 +451,7 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
         const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
         ProfScope ps(stream, fp64 ? 0 : 1, d, lflops);
         if (fp64) rc = cuda_err(launch_level_fp64(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
+        else if (small && small_kernel_kind() == 0) rc = cuda_err(launch_level_small_f32(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
         else if (small) rc = cuda_err(launch_level_tc_small(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
         else rc = cuda_err(launch_level_tc(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
         if (rc != STTSM_OK) return rc;

@@ -2,6 +2,8 @@
 // the FP32 -> BF16-piece split of X, and the plain FP64 level kernel of the
 // algorithm-by-blocks (Fig. 5 with Thm. 1).
 #include <cuda_bf16.h>
+#include <cstring>
+#include <mutex>
 #include "common.cuh"
 #include "launch.h"
 
@@ -145,6 +147,237 @@ int launch_split_x_batch(const SplitDesc* d_desc, int count, int blocks, int npi
     if (count <= 0 || blocks <= 0) return 0;
     split_x_batch_kernel<<<blocks, 256, 0, s>>>(d_desc, count, npiece);
     return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP32 small-contraction kernel
+
+// Level kernel for short contractions (n̄ b <= 64) in FP32 on the CUDA cores,
+// one thread per output row of a 128 x <=64 tile.  A CTA stages one tile at
+// a time in shared memory with cp.async (the tile's A rows, gathered from the
+// stored parent blocks through G / OFF with 16-byte copies where a row is
+// contiguous, and its X block); four CTAs share an SM, so the copies of one
+// overlap the arithmetic of the others.
+// The A operand is kept row-major per thread (stride 68 floats: one
+// conflict-free 16-byte read yields four contraction indices), X as
+// [kk][column] read by broadcast.  The column count of a tile selects a
+// compile-time width (8, 16, 24, 32, 48 or 64), so the inner loop has no
+// predicates.  Every entry is a sequential FP32 sum of <= 64 products.
+// Used where tensor-core tiles of <= 64 columns and <= 64 contraction indices
+// are latency-bound (batches and serving of small instances).
+constexpr int S32_ROWS = 128, S32_COLS = 64, S32_K = 64, S32_ASTRIDE = S32_K + 4;
+
+struct S32Stage {
+    float A[S32_ROWS][S32_ASTRIDE];   // A[t][kk]: operand row of output row row0 + t
+    float X[S32_K][S32_COLS];         // X[kk][c] = chi_{col0 + c, kk}, zero outside the tile / X
+};
+constexpr int S32_CTAS_PER_SM = 4;
+constexpr size_t S32_SMEM = sizeof(S32Stage);
+
+template <typename Desc>
+__device__ __forceinline__ const LevelInst& level_of(const Desc* d, int i);
+template <>
+__device__ __forceinline__ const LevelInst& level_of<LevelInst>(const LevelInst* d, int i) { return d[i]; }
+template <>
+__device__ __forceinline__ const LevelInst& level_of<TcInst>(const TcInst* d, int i) { return d[i].L; }
+
+__device__ __forceinline__ uint32_t s32_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void s32_cp4(uint32_t dst, const void* src, int bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(bytes));
+}
+__device__ __forceinline__ void s32_cp16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void s32_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void s32_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ int s32_width_class(int ncols)
+{
+    return ncols <= 8 ? 0 : ncols <= 16 ? 1 : ncols <= 24 ? 2 : ncols <= 32 ? 3 : ncols <= 48 ? 4 : 5;
+}
+
+// X block of a tile (zero-filled outside the tile and outside X).  Lane
+// t copies column t mod NCX (NCX = NC rounded up to a power of two) of rows
+// t / NCX, t / NCX + 128 / NCX, ...
+template <int NC>
+__device__ __forceinline__ void s32_issue_x(S32Stage& S, const LevelInst& I, const Tile& t, int Kc)
+{
+    constexpr int NCX = NC <= 8 ? 8 : NC <= 16 ? 16 : NC <= 32 ? 32 : 64;
+    constexpr int KSTEP = S32_ROWS / NCX;
+    const float* X = (const float*)I.X;
+    const int c = threadIdx.x & (NCX - 1);
+    const int j = t.col0 + c;
+    const bool colok = c < t.ncols && j < I.p;
+    const int nrows = colok ? (I.n < Kc ? I.n : Kc) : 0;
+    const int64_t pstep = (int64_t)KSTEP * I.p;
+    int kk = threadIdx.x / NCX;
+    const float* src = X + j + (int64_t)kk * I.p;
+    uint32_t dst = s32_smem(&S.X[kk][c]);
+    for (; kk < nrows; kk += KSTEP, src += pstep, dst += KSTEP * S32_COLS * 4) s32_cp4(dst, src, 4);
+    for (; kk < Kc; kk += KSTEP, dst += KSTEP * S32_COLS * 4) s32_cp4(dst, X, 0);
+}
+
+// Operand row of this thread: for every contraction block ib the stored
+// parent block rank(sort(prefix + ib)) and the insertion position q give the
+// entries off_q(rr) + a b^q, a = 0..b-1 (Thm. 1).
+__device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, const Tile& t, int Kc)
+{
+    float* Arow = S.A[threadIdx.x];
+    const int g = t.row0 + threadIdx.x;
+    if (g >= I.rows_per_parent) return;
+    const int R = I.R, b = I.b, nbar = I.nbar;
+    const int64_t bm = I.bm;
+    const int32_t* OFF = I.OFF;
+    const int pr = g / R, rr = g - pr * R;
+    const float* pbase = (const float*)I.parent + (int64_t)t.parent * I.P_parent * bm;
+    const int32_t* Grow = I.G + (int64_t)pr * nbar;
+    const bool vec = (b & 3) == 0;
+    // 16 contraction blocks per round (more only when b < 4); the table
+    // loads of a round are issued together
+    for (int ib0 = 0; ib0 < nbar; ib0 += S32_K / 4) {
+        int32_t gq[S32_K / 4];
+        int32_t off[S32_K / 4];
+#pragma unroll
+        for (int i = 0; i < S32_K / 4; ++i) gq[i] = ib0 + i < nbar ? __ldg(Grow + ib0 + i) : 0;
+#pragma unroll
+        for (int i = 0; i < S32_K / 4; ++i) off[i] = ib0 + i < nbar ? __ldg(OFF + (gq[i] & 7) * R + rr) : 0;
+#pragma unroll
+        for (int i = 0; i < S32_K / 4; ++i) {
+            if (ib0 + i >= nbar) break;
+            const int q = gq[i] & 7;
+            const float* src = pbase + (int64_t)(gq[i] >> 3) * bm + off[i];
+            float* dst = Arow + (ib0 + i) * b;
+            if (q == 0 && vec && ((uintptr_t)src & 15) == 0) {
+                for (int a = 0; a < b; a += 4) s32_cp16(s32_smem(dst + a), src + a);
+            } else {
+                const int stride = I.bpow[q];
+                const uint32_t d0 = s32_smem(dst);
+#pragma unroll 4
+                for (int a = 0; a < b; ++a) s32_cp4(d0 + 4 * a, src + (int64_t)a * stride, 4);
+            }
+        }
+    }
+    for (int kk = I.Ktot; kk < Kc; ++kk) Arow[kk] = 0.f;
+}
+
+template <typename Desc>
+__device__ __forceinline__ void s32_issue(S32Stage& S, const Desc* insts, const LevelInst& inst0, const Tile& t)
+{
+    const LevelInst& I = insts ? level_of(insts, t.inst) : inst0;
+    const int Kc = (I.Ktot + 3) & ~3;
+    s32_issue_a(S, I, t, Kc);
+    switch (s32_width_class(t.ncols)) {
+    case 0: s32_issue_x<8>(S, I, t, Kc); break;
+    case 1: s32_issue_x<16>(S, I, t, Kc); break;
+    case 2: s32_issue_x<24>(S, I, t, Kc); break;
+    case 3: s32_issue_x<32>(S, I, t, Kc); break;
+    case 4: s32_issue_x<48>(S, I, t, Kc); break;
+    default: s32_issue_x<64>(S, I, t, Kc); break;
+    }
+}
+
+// Row times the tile's X block, then the scatter into the children's blocks:
+// output (child cb + jb, block pr) at in-block offset OFF[k][rr] + b^k c.
+template <int NC>
+__device__ __forceinline__ void s32_compute_store(const S32Stage& S, const LevelInst& I, const Tile& t)
+{
+    const int g = t.row0 + threadIdx.x;
+    const int Kc = (I.Ktot + 3) & ~3;
+    float acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.f;
+    const float* Ar = S.A[threadIdx.x];
+#pragma unroll 2
+    for (int kk = 0; kk < Kc; kk += 4) {
+        const float4 a4 = *(const float4*)(Ar + kk);
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4* xr = (const float4*)S.X[kk + u];
+#pragma unroll
+            for (int c4 = 0; c4 < NC / 4; ++c4) {
+                const float4 x = xr[c4];
+                acc[4 * c4 + 0] = fmaf(av[u], x.x, acc[4 * c4 + 0]);
+                acc[4 * c4 + 1] = fmaf(av[u], x.y, acc[4 * c4 + 1]);
+                acc[4 * c4 + 2] = fmaf(av[u], x.z, acc[4 * c4 + 2]);
+                acc[4 * c4 + 3] = fmaf(av[u], x.w, acc[4 * c4 + 3]);
+            }
+        }
+    }
+    if (g >= I.rows_per_parent) return;
+    const int pr = g / I.R, rr = g - pr * I.R;
+    const int b = I.b, ncols = t.ncols;
+    const int bk = I.bpow[I.k];
+    const int64_t rowoff = __ldg(I.OFF + I.k * I.R + rr);
+    int jb = t.col0 / b, c = t.col0 - jb * b;
+    float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
+#pragma unroll
+    for (int e = 0; e < NC; ++e) {
+        if (e < ncols) dst[(int64_t)bk * c] = acc[e];
+        if (++c == b) { c = 0; dst += I.P_out * I.bm; }
+    }
+}
+
+template <typename Desc>
+__global__ void __launch_bounds__(S32_ROWS, S32_CTAS_PER_SM)
+level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Tile* __restrict__ tiles, int ntiles)
+{
+    extern __shared__ __align__(16) unsigned char s32_raw[];
+    S32Stage& S = *(S32Stage*)s32_raw;
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile t = tiles[ti];
+        const LevelInst& I = insts ? level_of(insts, t.inst) : inst0;
+        s32_issue(S, insts, inst0, t);
+        s32_commit();
+        s32_wait_all();
+        __syncthreads();
+        switch (s32_width_class(t.ncols)) {
+        case 0: s32_compute_store<8>(S, I, t); break;
+        case 1: s32_compute_store<16>(S, I, t); break;
+        case 2: s32_compute_store<24>(S, I, t); break;
+        case 3: s32_compute_store<32>(S, I, t); break;
+        case 4: s32_compute_store<48>(S, I, t); break;
+        default: s32_compute_store<64>(S, I, t); break;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename Desc>
+static int launch_small_f32(const Desc* d_insts, const LevelInst& inst0, const Tile* d_tiles, int ntiles, int num_sms,
+                            cudaStream_t s)
+{
+    if (ntiles <= 0) return 0;
+    static std::mutex mu;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            const cudaError_t e = cudaFuncSetAttribute(level_small_f32_kernel<Desc>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S32_SMEM);
+            if (e != cudaSuccess) return (int)e;
+            attr_set[dev] = true;
+        }
+    }
+    const int grid = ntiles < num_sms * S32_CTAS_PER_SM ? ntiles : num_sms * S32_CTAS_PER_SM;
+    level_small_f32_kernel<Desc><<<grid, S32_ROWS, S32_SMEM, s>>>(d_insts, inst0, d_tiles, ntiles);
+    return (int)cudaGetLastError();
+}
+
+int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
+                           int num_sms, cudaStream_t s)
+{
+    return launch_small_f32<LevelInst>(d_insts, inst0, d_tiles, ntiles, num_sms, s);
+}
+
+int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s)
+{
+    LevelInst none;
+    memset(&none, 0, sizeof(none));
+    return launch_small_f32<TcInst>(d_insts, none, d_tiles, ntiles, num_sms, s);
 }
 
 // ------------------------------------------------------------------ FP64 level kernel

@@ -38,6 +38,16 @@ constexpr int TC_KC = 32;
 int launch_level_tc(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
                     int num_sms, int* d_status, cudaStream_t s);
 
+// FP32 CUDA-core kernel for short contractions (n̄ b <= 64): tiles of 128 rows
+// x <= 64 columns, X read from the instance's FP32 X (LevelInst::X).
+int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
+                           int num_sms, cudaStream_t s);
+int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s);
+
+// Kernel for short contractions under the split precisions: 0 = FP32 CUDA-core
+// kernel (default), 1 = tcgen05 small-tile kernel (sttsm_set_small_kernel).
+int small_kernel_kind();
+
 // Small-tile variant: every tile has a contraction of at most TC_SMALL_K
 // (two stages) and at most TC_SMALL_BN columns; X maps with box rows 64.
 constexpr int TC_SMALL_K = 64;

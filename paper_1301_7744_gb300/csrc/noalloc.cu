@@ -152,6 +152,7 @@ extern "C" int sttsm_bcss_noalloc(const void* A, const void* X, int m, int64_t n
         const Tile* dt = (const Tile*)(base + tiles_off[d]);
         const int nt = (int)tiles[d].size();
         int lrc = fp64 ? launch_level_fp64(L, nullptr, dt, nt, sms, stream)
+                  : (small && small_kernel_kind() == 0) ? launch_level_small_f32(L, nullptr, dt, nt, sms, stream)
                   : small ? launch_level_tc_small(np, ti, nullptr, dt, nt, sms, status, stream)
                           : launch_level_tc(np, ti, nullptr, dt, nt, sms, status, stream);
         if (lrc != 0) return STTSM_ERR_CUDA;

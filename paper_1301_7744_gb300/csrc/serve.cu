@@ -301,6 +301,7 @@ int launch_step(sttsm_serve_s* H)
         const int n = (int)tiles[k].size();
         int lrc;
         if (k == 0) lrc = launch_level_tc(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, H->stream);
+        else if (k == 1 && small_kernel_kind() == 0) lrc = launch_level_small_f32_tc((const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->stream);
         else if (k == 1) lrc = launch_level_tc_small(H->np, dummy, (const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->status, H->stream);
         else lrc = launch_level_tma(H->np, tdummy, (const TmaInst*)(S.d + o_ti[k - 2]), dt, n, H->sms, H->status, k == 3, H->stream);
         if (lrc != 0) return STTSM_ERR_CUDA;

@@ -41,8 +41,16 @@ def make_batch(st, count, seed, fp64, cands=(4, 8, 16), small=True):
     return prec, insts, host
 
 
-@pytest.mark.parametrize("fp64", [False, True])
-def test_batch_equals_single_instance_runs(st, fp64):
+@pytest.mark.parametrize("fp64,kind", [(False, 0), (False, 1), (True, 0)])
+def test_batch_equals_single_instance_runs(st, fp64, kind):
+    st.sttsm_set_small_kernel(kind)
+    try:
+        _batch_equals_single(st, fp64)
+    finally:
+        st.sttsm_set_small_kernel(0)
+
+
+def _batch_equals_single(st, fp64):
     prec, insts, host = make_batch(st, 48, 3, fp64)
     plan = st.BatchPlan(insts, prec)
     ws = torch.empty(max(plan.workspace_size(), 1), dtype=torch.uint8, device="cuda")

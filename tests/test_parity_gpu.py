@@ -305,3 +305,21 @@ def test_argument_errors_do_not_launch(st):
     with pytest.raises(ValueError):
         st.sttsm_bcss(A.double(), X, m, n, p, b, C, st.STTSM_BF16X6, small)
     assert st.sttsm_device_status() == 0
+
+
+SMALL_SHAPES = [(3, 24, 24, 8), (3, 17, 5, 6), (4, 13, 9, 4), (5, 16, 16, 8), (6, 6, 5, 2), (5, 37, 29, 4),
+                (3, 40, 33, 1), (4, 30, 20, 3), (2, 64, 64, 1), (4, 21, 21, 7)]
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("m,n,p,b", SMALL_SHAPES)
+def test_small_contraction_kernels(st, kind, m, n, p, b):
+    """Contractions n̄ b <= 64 under BF16X6: FP32 CUDA-core kernel (0) and tcgen05 small tiles (1)."""
+    st.sttsm_set_small_kernel(kind)
+    try:
+        A, X = inputs(m, n, p, seed_a=3 * m + n, seed_x=p, fp32=True)
+        Ab = device_bcss_from_dense(st, A, m, n, b, torch.float32)
+        got = run_sttsm(st, Ab, X, m, n, p, b, st.STTSM_BF16X6)
+    finally:
+        st.sttsm_set_small_kernel(0)
+    assert rel_fro(got, oracle_C_bcss(A, X, m, p, b)) <= 1e-6

@@ -75,7 +75,7 @@ def emulate(st, m, n, p, b, prec, A_bcss, X):
 
 
 CASES = [(3, 24, 24, 8), (1, 10, 7, 4), (2, 9, 11, 3), (3, 17, 5, 6), (4, 13, 9, 4), (5, 7, 6, 2), (4, 20, 12, 5),
-         (3, 40, 40, 4), (2, 300, 260, 64), (6, 6, 5, 2)]
+         (3, 40, 40, 4), (2, 300, 260, 64), (6, 6, 5, 2), (3, 40, 33, 1), (2, 64, 64, 1), (4, 21, 21, 7)]
 
 
 @pytest.mark.parametrize("m,n,p,b", CASES)
