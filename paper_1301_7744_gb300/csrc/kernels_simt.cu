@@ -156,7 +156,8 @@ int launch_split_x_batch(const SplitDesc* d_desc, int count, int blocks, int npi
 // a time in shared memory with cp.async (the tile's A rows, gathered from the
 // stored parent blocks through G / OFF with 16-byte copies where a row is
 // contiguous, and its X block); four CTAs share an SM, so the copies of one
-// overlap the arithmetic of the others.
+// overlap the arithmetic of the others.  A CTA copies an X block only when
+// it differs from the one of its previous tile.
 // The A operand is kept row-major per thread (stride 68 floats: one
 // conflict-free 16-byte read yields four contraction indices), X as
 // [kk][column] read by broadcast.  The column count of a tile selects a
@@ -218,15 +219,42 @@ __device__ __forceinline__ void s32_issue_x(S32Stage& S, const LevelInst& I, con
     for (; kk < Kc; kk += KSTEP, dst += KSTEP * S32_COLS * 4) s32_cp4(dst, X, 0);
 }
 
+// b entries of one contraction block, stride b^q (compile-time for B > 0)
+template <int B, int STRIDE>
+__device__ __forceinline__ void s32_copy_block(uint32_t dst, const float* src)
+{
+#pragma unroll
+    for (int a = 0; a < B; ++a) s32_cp4(dst + 4 * a, src + a * STRIDE, 4);
+}
+
+template <int B>
+__device__ __forceinline__ void s32_copy_q(uint32_t dst, const float* src, int q)
+{
+    switch (q) {
+    case 1: s32_copy_block<B, B>(dst, src); break;
+    case 2: s32_copy_block<B, B * B>(dst, src); break;
+    case 3: s32_copy_block<B, B * B * B>(dst, src); break;
+    case 4: s32_copy_block<B, B * B * B * B>(dst, src); break;
+    default: {
+        int stride = 1;
+        for (int i = 0; i < q; ++i) stride *= B;
+#pragma unroll
+        for (int a = 0; a < B; ++a) s32_cp4(dst + 4 * a, src + (int64_t)a * stride, 4);
+    }
+    }
+}
+
 // Operand row of this thread: for every contraction block ib the stored
 // parent block rank(sort(prefix + ib)) and the insertion position q give the
-// entries off_q(rr) + a b^q, a = 0..b-1 (Thm. 1).
+// entries off_q(rr) + a b^q, a = 0..b-1 (Thm. 1).  B > 0: b == B (strides
+// known at compile time); B == 0: any b.
+template <int B>
 __device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, const Tile& t, int Kc)
 {
     float* Arow = S.A[threadIdx.x];
     const int g = t.row0 + threadIdx.x;
     if (g >= I.rows_per_parent) return;
-    const int R = I.R, b = I.b, nbar = I.nbar;
+    const int R = I.R, b = B > 0 ? B : I.b, nbar = I.nbar;
     const int64_t bm = I.bm;
     const int32_t* OFF = I.OFF;
     const int pr = g / R, rr = g - pr * R;
@@ -249,7 +277,14 @@ __device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, con
             const float* src = pbase + (int64_t)(gq[i] >> 3) * bm + off[i];
             float* dst = Arow + (ib0 + i) * b;
             if (q == 0 && vec && ((uintptr_t)src & 15) == 0) {
-                for (int a = 0; a < b; a += 4) s32_cp16(s32_smem(dst + a), src + a);
+#pragma unroll
+                for (int a = 0; a < (B > 0 ? B : S32_K); a += 4) {
+                    if (B == 0 && a >= b) break;
+                    s32_cp16(s32_smem(dst + a), src + a);
+                }
+            } else if (B > 0) {
+                if (q == 0) s32_copy_block<(B > 0 ? B : 1), 1>(s32_smem(dst), src);
+                else s32_copy_q<(B > 0 ? B : 1)>(s32_smem(dst), src, q);
             } else {
                 const int stride = I.bpow[q];
                 const uint32_t d0 = s32_smem(dst);
@@ -262,11 +297,18 @@ __device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, con
 }
 
 template <typename Desc>
-__device__ __forceinline__ void s32_issue(S32Stage& S, const Desc* insts, const LevelInst& inst0, const Tile& t)
+__device__ __forceinline__ void s32_issue(S32Stage& S, const Desc* insts, const LevelInst& inst0, const Tile& t,
+                                          bool with_x)
 {
     const LevelInst& I = insts ? level_of(insts, t.inst) : inst0;
     const int Kc = (I.Ktot + 3) & ~3;
-    s32_issue_a(S, I, t, Kc);
+    switch (I.b) {
+    case 4: s32_issue_a<4>(S, I, t, Kc); break;
+    case 8: s32_issue_a<8>(S, I, t, Kc); break;
+    case 16: s32_issue_a<16>(S, I, t, Kc); break;
+    default: s32_issue_a<0>(S, I, t, Kc); break;
+    }
+    if (!with_x) return;
     switch (s32_width_class(t.ncols)) {
     case 0: s32_issue_x<8>(S, I, t, Kc); break;
     case 1: s32_issue_x<16>(S, I, t, Kc); break;
@@ -325,10 +367,15 @@ level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Ti
 {
     extern __shared__ __align__(16) unsigned char s32_raw[];
     S32Stage& S = *(S32Stage*)s32_raw;
+    // row groups of one parent node share their X block; it stays in shared
+    // memory while the CTA's next tile has the same one
+    int x_inst = -1, x_col0 = -1, x_ncols = -1;
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile t = tiles[ti];
         const LevelInst& I = insts ? level_of(insts, t.inst) : inst0;
-        s32_issue(S, insts, inst0, t);
+        const bool new_x = t.inst != x_inst || t.col0 != x_col0 || t.ncols != x_ncols;
+        x_inst = t.inst; x_col0 = t.col0; x_ncols = t.ncols;
+        s32_issue(S, insts, inst0, t, new_x);
         s32_commit();
         s32_wait_all();
         __syncthreads();
