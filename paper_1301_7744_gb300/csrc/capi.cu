@@ -156,6 +156,35 @@ int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, i
     for (int a = 0; a < m - 1; ++a) R *= b;
     const int64_t bm = R * b;
     int64_t bq = 1;
+    if (b == 16) {
+        // one stored block per 16-wide K slice, 32-byte swizzle
+        for (int q = 0; q <= k; ++q, bq *= b) {
+            CUresult r;
+            if (q == 0) {
+                // K-major: {a (contiguous), rows (b apart), block x piece}
+                cuuint64_t dims[3] = {(cuuint64_t)b, (cuuint64_t)R, (cuuint64_t)(nblocks * npiece)};
+                cuuint64_t strides[2] = {(cuuint64_t)b * 2, (cuuint64_t)bm * 2};
+                cuuint32_t box[3] = {16, 128, (cuuint32_t)npiece};
+                cuuint32_t estr[3] = {1, 1, 1};
+                r = enc(&maps[0], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(pieces), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            } else {
+                // MN-major: {16 rows (contiguous), a (b^q apart), 16-row atoms, outer rows (b^(q+1) apart), block x piece}
+                cuuint64_t dims[5] = {16, (cuuint64_t)b, (cuuint64_t)(bq / 16), (cuuint64_t)(R / bq),
+                                      (cuuint64_t)(nblocks * npiece)};
+                cuuint64_t strides[4] = {(cuuint64_t)bq * 2, 32, (cuuint64_t)bq * b * 2, (cuuint64_t)bm * 2};
+                cuuint32_t box[5] = {16, 16, (cuuint32_t)((bq < 128 ? bq : 128) / 16), (cuuint32_t)(bq < 128 ? 128 / bq : 1),
+                                     (cuuint32_t)npiece};
+                cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+                r = enc(&maps[q], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(pieces), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            }
+            if (r != CUDA_SUCCESS) return STTSM_ERR_CUDA;
+        }
+        return STTSM_OK;
+    }
     for (int q = 0; q <= k; ++q, bq *= b) {
         CUresult r;
         if (q == 0) {

@@ -5,7 +5,8 @@
 // The operands are those of level_tc_kernel (kernels_tc.cu): rows of stored
 // parent blocks gathered through G times X.  Here the parent temporaries (and A,
 // pre-split once) are stored as BF16 pieces, [node][block][piece][b^m], so every
-// 32-wide contraction stage of a 128-row tile is one box of one stored block:
+// 32-wide contraction stage of a 128-row tile is one box of one stored block
+// (b = 16: two boxes, one per 16-wide MMA slice, in 32-byte swizzle):
 //   * insertion position q = 0: the contraction index is the block's fastest
 //     mode, rows are b apart -> a 3-D K-major box {32, 128, NP};
 //   * q >= 1: rows are contiguous in runs of b^q >= 32 and the contraction index
@@ -108,23 +109,46 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const LevelInst& I = TI.L;
                 const int pr = t.row0 / I.R, rr0 = t.row0 - pr * I.R;
                 const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
-                const int nk = I.Ktot / TC_KC;
+                const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
+                const bool b16 = I.b == 16;
                 for (int ks = 0; ks < nk; ++ks) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
-                    const int k0 = ks * TC_KC, ib = k0 / I.b, a0 = k0 - ib * I.b;
-                    const int32_t gq = __ldg(Grow + ib);
-                    const int q = gq & 7;
-                    const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
+                    const int k0 = ks * TC_KC;
                     const uint32_t sA = smem_u32(smem + stage * S::STAGE);
                     const uint32_t sB = sA + NP * S::A_PLANE;
                     // X box rows: the smallest of 256 / 128 / 64 that covers the tile's columns
                     const int xsel = t.ncols > 128 ? 0 : (t.ncols > 64 ? 1 : 2);
-                    mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(NP * S::A_PLANE + (NP * S::B_PLANE >> xsel)));
-                    if (q == 0) {
-                        tma_load_3d(sA, &TI.tmA[0], a0, rr0, bp, full_bar(stage));
+                    if (b16) {
+                        // two stored blocks per stage, one per 16-wide K slice (the
+                        // second is absent in the last stage when n-bar is odd)
+                        const int ib0 = k0 >> 4;
+                        const int nblk = ib0 + 1 < I.nbar ? 2 : 1;
+                        mbar_arrive_expect_tx(full_bar(stage),
+                                              (uint32_t)(nblk * NP * (S::A_PLANE / 2) + (NP * S::B_PLANE >> xsel)));
+                        for (int h = 0; h < nblk; ++h) {
+                            const int32_t gq = __ldg(Grow + ib0 + h);
+                            const int q = gq & 7;
+                            const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
+                            const uint32_t dA = sA + (uint32_t)(h * NP * (S::A_PLANE / 2));
+                            if (q == 0) {
+                                tma_load_3d(dA, &TI.tmA[0], 0, rr0, bp, full_bar(stage));
+                            } else {
+                                const int bq = I.bpow[q];
+                                tma_load_5d(dA, &TI.tmA[q], 0, 0, (rr0 % bq) >> 4, rr0 / bq, bp, full_bar(stage));
+                            }
+                        }
                     } else {
-                        const int bq = I.bpow[q];
-                        tma_load_5d(sA, &TI.tmA[q], 0, a0, (rr0 % bq) >> 5, rr0 / bq, bp, full_bar(stage));
+                        const int ib = k0 / I.b, a0 = k0 - ib * I.b;
+                        const int32_t gq = __ldg(Grow + ib);
+                        const int q = gq & 7;
+                        const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
+                        mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(NP * S::A_PLANE + (NP * S::B_PLANE >> xsel)));
+                        if (q == 0) {
+                            tma_load_3d(sA, &TI.tmA[0], a0, rr0, bp, full_bar(stage));
+                        } else {
+                            const int bq = I.bpow[q];
+                            tma_load_5d(sA, &TI.tmA[q], 0, a0, (rr0 % bq) >> 5, rr0 / bq, bp, full_bar(stage));
+                        }
                     }
                     tma_load_3d(sB, &TI.tmX[xsel], k0, t.col0, 0, full_bar(stage));
                     last_stage = stage;
@@ -151,7 +175,8 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const LevelInst& I = TI.L;
                 const int pr = t.row0 / I.R;
                 const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
-                const int nk = I.Ktot / TC_KC;
+                const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
+                const bool b16 = I.b == 16;
                 const int nmma = (t.ncols + 15) & ~15;
                 const uint32_t idesc_k = idesc_bf16(nmma), idesc_mn = idesc_bf16_amn(nmma);
                 // B piece planes are as tall as the X box the producer used
@@ -161,19 +186,35 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 tile_phase ^= 1u;
                 tc_fence_after();
                 for (int ks = 0; ks < nk; ++ks) {
-                    const int ib = (ks * TC_KC) / I.b;
-                    const bool mn = (__ldg(Grow + ib) & 7) != 0;
+                    // A major-ness and presence of the two 16-wide K slices of the stage
+                    bool mnk[2], valid[2];
+                    if (b16) {
+                        const int ib0 = ks * 2;
+                        valid[0] = true;
+                        valid[1] = ib0 + 1 < I.nbar;
+                        mnk[0] = (__ldg(Grow + ib0) & 7) != 0;
+                        mnk[1] = valid[1] && (__ldg(Grow + ib0 + 1) & 7) != 0;
+                    } else {
+                        const int ib = (ks * TC_KC) / I.b;
+                        mnk[0] = mnk[1] = (__ldg(Grow + ib) & 7) != 0;
+                        valid[0] = valid[1] = true;
+                    }
                     if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sA = smem_u32(smem + stage * S::STAGE);
                     const uint32_t sB = sA + NP * S::A_PLANE;
-                    const uint32_t idesc = mn ? idesc_mn : idesc_k;
                     auto adesc = [&](int s, int kh) {
-                        return mn ? smem_desc_sw64_mn(sA + s * S::A_PLANE + kh * 1024)
-                                  : smem_desc_sw64(sA + s * S::A_PLANE + kh * 32);
+                        if (b16) {
+                            const uint32_t a = sA + (uint32_t)((kh * NP + s) * (S::A_PLANE / 2));
+                            return mnk[kh] ? smem_desc_sw32_mn(a) : smem_desc_sw32(a);
+                        }
+                        return mnk[kh] ? smem_desc_sw64_mn(sA + s * S::A_PLANE + kh * 1024)
+                                       : smem_desc_sw64(sA + s * S::A_PLANE + kh * 32);
                     };
 #pragma unroll
                     for (int kh = 0; kh < TC_KC / 16; ++kh) {
+                        if (!valid[kh]) continue;
+                        const uint32_t idesc = mnk[kh] ? idesc_mn : idesc_k;
 #pragma unroll
                         for (int s = 0; s < NP; ++s) {
 #pragma unroll
@@ -194,7 +235,9 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     }
 #pragma unroll
                     for (int kh = 0; kh < TC_KC / 16; ++kh)
-                        tc_mma(tmem_d0, adesc(0, kh), smem_desc_sw64(sB + kh * 32), idesc, (group_start && kh == 0) ? 0u : 1u);
+                        if (valid[kh])
+                            tc_mma(tmem_d0, adesc(0, kh), smem_desc_sw64(sB + kh * 32), mnk[kh] ? idesc_mn : idesc_k,
+                                   (group_start && kh == 0) ? 0u : 1u);
                     tc_commit(empty_bar(stage));
                     if ((ks % T_GS) == T_GS - 1 || ks == nk - 1) tc_commit(d0_full);
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -232,7 +275,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             const Tile t = tiles[ti];
             const TmaInst& TI = insts ? insts[t.inst] : inst0;
             const LevelInst& I = TI.L;
-            const int nk = I.Ktot / TC_KC;
+            const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
             const int ngroups = (nk + T_GS - 1) / T_GS;
             const bool active = colbase < t.ncols;
 #pragma unroll

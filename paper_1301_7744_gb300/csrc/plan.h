@@ -37,7 +37,7 @@ inline bool tc_small_mode(const Shape& s) { return s.nbar * s.b <= 64; }
 // Split-precision shapes whose block size is a multiple of 32 and whose
 // output blocks hold a multiple of 128 rows take the TMA-fed kernel
 // (temporaries stored as BF16 pieces).
-inline bool tc_tma_mode(const Shape& s) { return !tc_small_mode(s) && s.b % 32 == 0 && s.R % 128 == 0; }
+inline bool tc_tma_mode(const Shape& s) { return !tc_small_mode(s) && (s.b % 32 == 0 || s.b == 16) && s.R % 128 == 0; }
 
 // Host tile list and G table of level d (appended to the given vectors).
 // Tiles cover, for every parent node, P_out * R rows in steps of BM and the

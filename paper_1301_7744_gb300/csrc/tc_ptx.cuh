@@ -165,6 +165,33 @@ __device__ __forceinline__ uint64_t smem_desc_sw64_mn(uint32_t addr)
     return d;
 }
 
+// K-major SW32 operand (16 BF16 of K per 32-byte row): 8-row groups 256 B
+// apart; one 16-wide K slice per descriptor.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(256 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
+    return d;
+}
+
+// MN-major SW32 operand: 16-element (32-byte) M atoms of 16 K-rows each,
+// atoms 512 B apart (leading byte offset), 8-row K groups 256 B apart
+// (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc_sw32_mn(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(512 >> 4) << 16;
+    d |= (uint64_t)(256 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
+    return d;
+}
+
 // kind::f16 instruction descriptor with an MN-major A operand (bit 15).
 __device__ __forceinline__ uint32_t idesc_bf16_amn(int n)
 {

@@ -121,7 +121,8 @@ def test_config1_rank2_closed_form(st, precname):
 
 
 SHAPES = [(1, 10, 7, 4), (2, 9, 11, 3), (2, 130, 70, 32), (3, 17, 5, 6), (3, 40, 40, 4), (3, 100, 100, 32),
-          (3, 96, 96, 48), (4, 13, 9, 4), (4, 20, 12, 5), (5, 7, 6, 2), (5, 16, 16, 8), (6, 6, 5, 2), (3, 130, 130, 64)]
+          (3, 96, 96, 48), (4, 13, 9, 4), (4, 20, 12, 5), (5, 7, 6, 2), (5, 16, 16, 8), (6, 6, 5, 2), (3, 130, 130, 64),
+          (3, 100, 90, 16), (3, 70, 130, 16), (3, 144, 40, 16), (4, 70, 40, 16)]
 
 
 @pytest.mark.parametrize("m,n,p,b", SHAPES)
@@ -133,6 +134,21 @@ def test_shapes(st, m, n, p, b, precname):
     ref = oracle_C_bcss(A, X, m, p, b)
     assert not np.isnan(got).any()
     assert rel_fro(got, ref) <= TOL[precname]
+
+
+@pytest.mark.parametrize("m,n,p,b", [(3, 100, 90, 16), (4, 70, 40, 16), (3, 96, 96, 32)])
+def test_tma_path_taken(st, m, n, p, b):
+    """b = 16 (n-bar odd or even) and multiples of 32 run on the TMA-fed level kernel."""
+    A, X = inputs(m, n, p, seed_a=5, seed_x=6, fp32=True)
+    Ab = device_bcss_from_dense(st, A, m, n, b, torch.float32)
+    st.sttsm_profile_enable(True)
+    try:
+        got = run_sttsm(st, Ab, X, m, n, p, b, st.STTSM_BF16X6)
+        kinds = [r["kind"] for r in st.sttsm_profile_read()]
+    finally:
+        st.sttsm_profile_enable(False)
+    assert kinds.count("tma") == m
+    assert rel_fro(got, oracle_C_bcss(A, X, m, p, b)) <= TOL["bf16x6"]
 
 
 def test_bf16x3_two_piece_error_is_reported(st):
