@@ -154,21 +154,21 @@ int launch_split_x_batch(const SplitDesc* d_desc, int count, int blocks, int npi
 // Level kernel for short contractions (n̄ b <= 64) in FP32 on the CUDA cores,
 // one thread per output row of a 128 x <=64 tile.  A CTA stages one tile at
 // a time in shared memory with cp.async (the tile's A rows, gathered from the
-// stored parent blocks through G / OFF with 16-byte copies where a row is
-// contiguous, and its X block); four CTAs share an SM, so the copies of one
+// stored parent blocks through G / OFF, and its X block); four CTAs share an SM, so the copies of one
 // overlap the arithmetic of the others.  A CTA copies an X block only when
 // it differs from the one of its previous tile.
-// The A operand is kept row-major per thread (stride 68 floats: one
-// conflict-free 16-byte read yields four contraction indices), X as
-// [kk][column] read by broadcast.  The column count of a tile selects a
+// Both operands are kept [kk][...] in shared memory: A[kk][row] (the 4-byte
+// copies of 32 rows and the reads of a contraction row are conflict-free),
+// X[kk][column] read by broadcast.  The column count of a tile selects a
 // compile-time width (8, 16, 24, 32, 48 or 64), so the inner loop has no
-// predicates.  Every entry is a sequential FP32 sum of <= 64 products.
+// predicates, and a register blocking (1, 2 or 4 rows per thread) that
+// lets one X read feed several rows.  Every entry is a sequential FP32 sum of <= 64 products.
 // Used where tensor-core tiles of <= 64 columns and <= 64 contraction indices
 // are latency-bound (batches and serving of small instances).
-constexpr int S32_ROWS = 128, S32_COLS = 64, S32_K = 64, S32_ASTRIDE = S32_K + 4;
+constexpr int S32_ROWS = 128, S32_COLS = 64, S32_K = 64;
 
 struct S32Stage {
-    float A[S32_ROWS][S32_ASTRIDE];   // A[t][kk]: operand row of output row row0 + t
+    float A[S32_K][S32_ROWS];         // A[kk][t]: operand of output row row0 + t
     float X[S32_K][S32_COLS];         // X[kk][c] = chi_{col0 + c, kk}, zero outside the tile / X
 };
 constexpr int S32_CTAS_PER_SM = 4;
@@ -185,10 +185,6 @@ __device__ __forceinline__ uint32_t s32_smem(const void* p) { return (uint32_t)_
 __device__ __forceinline__ void s32_cp4(uint32_t dst, const void* src, int bytes)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(bytes));
-}
-__device__ __forceinline__ void s32_cp16(uint32_t dst, const void* src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
 }
 __device__ __forceinline__ void s32_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void s32_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -219,12 +215,14 @@ __device__ __forceinline__ void s32_issue_x(S32Stage& S, const LevelInst& I, con
     for (; kk < Kc; kk += KSTEP, dst += KSTEP * S32_COLS * 4) s32_cp4(dst, X, 0);
 }
 
-// b entries of one contraction block, stride b^q (compile-time for B > 0)
+// b entries of one contraction block (source stride b^q, compile-time for
+// B > 0) into consecutive contraction rows of the stage
+constexpr int S32_KROW = S32_ROWS * 4;   // bytes between contraction rows of A
 template <int B, int STRIDE>
 __device__ __forceinline__ void s32_copy_block(uint32_t dst, const float* src)
 {
 #pragma unroll
-    for (int a = 0; a < B; ++a) s32_cp4(dst + 4 * a, src + a * STRIDE, 4);
+    for (int a = 0; a < B; ++a) s32_cp4(dst + S32_KROW * a, src + a * STRIDE, 4);
 }
 
 template <int B>
@@ -239,7 +237,7 @@ __device__ __forceinline__ void s32_copy_q(uint32_t dst, const float* src, int q
         int stride = 1;
         for (int i = 0; i < q; ++i) stride *= B;
 #pragma unroll
-        for (int a = 0; a < B; ++a) s32_cp4(dst + 4 * a, src + (int64_t)a * stride, 4);
+        for (int a = 0; a < B; ++a) s32_cp4(dst + S32_KROW * a, src + (int64_t)a * stride, 4);
     }
     }
 }
@@ -251,7 +249,6 @@ __device__ __forceinline__ void s32_copy_q(uint32_t dst, const float* src, int q
 template <int B>
 __device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, const Tile& t, int Kc)
 {
-    float* Arow = S.A[threadIdx.x];
     const int g = t.row0 + threadIdx.x;
     if (g >= I.rows_per_parent) return;
     const int R = I.R, b = B > 0 ? B : I.b, nbar = I.nbar;
@@ -260,7 +257,6 @@ __device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, con
     const int pr = g / R, rr = g - pr * R;
     const float* pbase = (const float*)I.parent + (int64_t)t.parent * I.P_parent * bm;
     const int32_t* Grow = I.G + (int64_t)pr * nbar;
-    const bool vec = (b & 3) == 0;
     // 16 contraction blocks per round (more only when b < 4); the table
     // loads of a round are issued together
     for (int ib0 = 0; ib0 < nbar; ib0 += S32_K / 4) {
@@ -275,25 +271,18 @@ __device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, con
             if (ib0 + i >= nbar) break;
             const int q = gq[i] & 7;
             const float* src = pbase + (int64_t)(gq[i] >> 3) * bm + off[i];
-            float* dst = Arow + (ib0 + i) * b;
-            if (q == 0 && vec && ((uintptr_t)src & 15) == 0) {
-#pragma unroll
-                for (int a = 0; a < (B > 0 ? B : S32_K); a += 4) {
-                    if (B == 0 && a >= b) break;
-                    s32_cp16(s32_smem(dst + a), src + a);
-                }
-            } else if (B > 0) {
-                if (q == 0) s32_copy_block<(B > 0 ? B : 1), 1>(s32_smem(dst), src);
-                else s32_copy_q<(B > 0 ? B : 1)>(s32_smem(dst), src, q);
+            const uint32_t d0 = s32_smem(&S.A[(ib0 + i) * b][threadIdx.x]);
+            if (B > 0) {
+                if (q == 0) s32_copy_block<(B > 0 ? B : 1), 1>(d0, src);
+                else s32_copy_q<(B > 0 ? B : 1)>(d0, src, q);
             } else {
                 const int stride = I.bpow[q];
-                const uint32_t d0 = s32_smem(dst);
 #pragma unroll 4
-                for (int a = 0; a < b; ++a) s32_cp4(d0 + 4 * a, src + (int64_t)a * stride, 4);
+                for (int a = 0; a < b; ++a) s32_cp4(d0 + S32_KROW * a, src + (int64_t)a * stride, 4);
             }
         }
     }
-    for (int kk = I.Ktot; kk < Kc; ++kk) Arow[kk] = 0.f;
+    for (int kk = I.Ktot; kk < Kc; ++kk) S.A[kk][threadIdx.x] = 0.f;
 }
 
 template <typename Desc>
@@ -319,45 +308,61 @@ __device__ __forceinline__ void s32_issue(S32Stage& S, const Desc* insts, const 
     }
 }
 
-// Row times the tile's X block, then the scatter into the children's blocks:
+// Rows times the tile's X block, then the scatter into the children's blocks:
 // output (child cb + jb, block pr) at in-block offset OFF[k][rr] + b^k c.
-template <int NC>
+// A thread computes TR rows (t mod 128/TR, + 128/TR, ...) times NC/TR columns
+// (part t / (128/TR)), so every X value read from shared memory feeds TR
+// products.
+template <int NC, int TR>
 __device__ __forceinline__ void s32_compute_store(const S32Stage& S, const LevelInst& I, const Tile& t)
 {
-    const int g = t.row0 + threadIdx.x;
+    constexpr int TC = NC / TR, RSTEP = S32_ROWS / TR;
+    const int r0 = threadIdx.x % RSTEP, part = threadIdx.x / RSTEP;
     const int Kc = (I.Ktot + 3) & ~3;
-    float acc[NC];
+    float acc[TR][TC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.f;
-    const float* Ar = S.A[threadIdx.x];
+    for (int j = 0; j < TR; ++j)
+#pragma unroll
+        for (int c = 0; c < TC; ++c) acc[j][c] = 0.f;
 #pragma unroll 2
     for (int kk = 0; kk < Kc; kk += 4) {
-        const float4 a4 = *(const float4*)(Ar + kk);
-        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+        float av[4][TR];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < TR; ++j) av[u][j] = S.A[kk + u][r0 + j * RSTEP];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float4* xr = (const float4*)S.X[kk + u];
+            const float4* xr = (const float4*)&S.X[kk + u][part * TC];
 #pragma unroll
-            for (int c4 = 0; c4 < NC / 4; ++c4) {
+            for (int c4 = 0; c4 < TC / 4; ++c4) {
                 const float4 x = xr[c4];
-                acc[4 * c4 + 0] = fmaf(av[u], x.x, acc[4 * c4 + 0]);
-                acc[4 * c4 + 1] = fmaf(av[u], x.y, acc[4 * c4 + 1]);
-                acc[4 * c4 + 2] = fmaf(av[u], x.z, acc[4 * c4 + 2]);
-                acc[4 * c4 + 3] = fmaf(av[u], x.w, acc[4 * c4 + 3]);
+#pragma unroll
+                for (int j = 0; j < TR; ++j) {
+                    acc[j][4 * c4 + 0] = fmaf(av[u][j], x.x, acc[j][4 * c4 + 0]);
+                    acc[j][4 * c4 + 1] = fmaf(av[u][j], x.y, acc[j][4 * c4 + 1]);
+                    acc[j][4 * c4 + 2] = fmaf(av[u][j], x.z, acc[j][4 * c4 + 2]);
+                    acc[j][4 * c4 + 3] = fmaf(av[u][j], x.w, acc[j][4 * c4 + 3]);
+                }
             }
         }
     }
-    if (g >= I.rows_per_parent) return;
-    const int pr = g / I.R, rr = g - pr * I.R;
-    const int b = I.b, ncols = t.ncols;
-    const int bk = I.bpow[I.k];
-    const int64_t rowoff = __ldg(I.OFF + I.k * I.R + rr);
-    int jb = t.col0 / b, c = t.col0 - jb * b;
-    float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
+    const int b = I.b, bk = I.bpow[I.k];
+    const int cfirst = t.col0 + part * TC;
+    const int nvalid = t.ncols - part * TC;
 #pragma unroll
-    for (int e = 0; e < NC; ++e) {
-        if (e < ncols) dst[(int64_t)bk * c] = acc[e];
-        if (++c == b) { c = 0; dst += I.P_out * I.bm; }
+    for (int j = 0; j < TR; ++j) {
+        const int g = t.row0 + r0 + j * RSTEP;
+        if (g >= I.rows_per_parent) continue;
+        const int pr = g / I.R, rr = g - pr * I.R;
+        const int64_t rowoff = __ldg(I.OFF + I.k * I.R + rr);
+        int jb = cfirst / b, c = cfirst - jb * b;
+        float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
+#pragma unroll
+        for (int e = 0; e < TC; ++e) {
+            if (e < nvalid) dst[(int64_t)bk * c] = acc[j][e];
+            if (++c == b) { c = 0; dst += I.P_out * I.bm; }
+        }
     }
 }
 
@@ -380,12 +385,12 @@ level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Ti
         s32_wait_all();
         __syncthreads();
         switch (s32_width_class(t.ncols)) {
-        case 0: s32_compute_store<8>(S, I, t); break;
-        case 1: s32_compute_store<16>(S, I, t); break;
-        case 2: s32_compute_store<24>(S, I, t); break;
-        case 3: s32_compute_store<32>(S, I, t); break;
-        case 4: s32_compute_store<48>(S, I, t); break;
-        default: s32_compute_store<64>(S, I, t); break;
+        case 0: s32_compute_store<8, 1>(S, I, t); break;
+        case 1: s32_compute_store<16, 2>(S, I, t); break;
+        case 2: s32_compute_store<24, 2>(S, I, t); break;
+        case 3: s32_compute_store<32, 2>(S, I, t); break;
+        case 4: s32_compute_store<48, 4>(S, I, t); break;
+        default: s32_compute_store<64, 4>(S, I, t); break;
         }
         __syncthreads();
     }
