@@ -52,8 +52,9 @@ def parse_args():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
-                    help="single: m=3 n=p=768 instance (default); batch: 4096 mixed instances; serve: Poisson stream")
+    ap.add_argument("--workload", default="single", choices=["single", "m4", "batch", "serve"],
+                    help="single: m=3 n=p=768 instance (default); m4: m=4 n=128 p=64 compressing instance; "
+                         "batch: 4096 mixed instances; serve: Poisson stream")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--ws-gb", type=float, default=48.0, help="batch workspace budget (GiB)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -332,7 +333,93 @@ def check_and_baseline(args, C, C64, Xh, X32, b, F, world):
         cpu_base = {"value": F * S / P / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_threads(), "kind": "oracle",
                     "sample": "FP64 oracle dense mode-product chain (A x_2 X_S x_1 X x_0 X) for %d of %d "
                               "slices C[:,:,j], %.1f s; value = BCSS flop count x %d/%d / time" % (S, P, dt, S, P)}
+        one = oracle_one_core(2)
+        if one:
+            cpu_base["one_core"] = {"value": F * 2 / P / one / 1e12, "unit": "TFLOP/s", "cores": 1,
+                                    "sample": "same chain, 2 slices, %.1f s, OMP_NUM_THREADS=1 in a child process" % one}
     return rel_err, cpu_base
+
+
+def oracle_one_core(slices):
+    """The same oracle chain on one host core (a child process started with
+    OMP_NUM_THREADS=1, since the thread count is fixed at the first parallel
+    region); returns seconds for `slices` slices, or None on failure."""
+    code = ("import sys, time, numpy as np; sys.path.insert(0, %r); import synth, oracle; oracle.build(); "
+            "A = synth.sym_uniform_dense(%d, %d, %d); "
+            "X = synth.x_gaussian(%d, %d, %d).astype(np.float32).astype(np.float64); "
+            "rows = np.random.default_rng(%d).integers(0, %d, size=%d); t0 = time.perf_counter(); "
+            "oracle.ttm_chain(A, [X, X, X[rows]], %d); print(time.perf_counter() - t0)"
+            % (ROOT, M, N, SEED_A, SEED_X, P, N, SEED_J + 1, P, slices, M))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+
+
+def bcss_pos_m(j, b, m):
+    import math
+    s = sorted(int(x) for x in j)
+    rank = sum(math.comb(s[t] // b + t, t + 1) for t in range(m))
+    return rank * b ** m + sum((s[t] % b) * b ** t for t in range(m))
+
+
+def run_m4(args):
+    """The compressing single instance m = 4, n = 128, p = 64 (X with orthonormal
+    rows), b in {8, 16, 32}, BF16X6 and FP64: TFLOP/s per (b, precision) and the
+    error of 64 sampled C entries against the FP64 oracle."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_7744_gb300 as st
+    import synth
+    import oracle
+    m, n, p = 4, 128, 64
+    stream = torch.cuda.current_stream().cuda_stream
+    Xh = synth.x_orthonormal_rows(SEED_X, p, n)
+    X32 = Xh.astype(np.float32).astype(np.float64)
+    steps, warm = max(3, min(args.steps, 50)), max(3, args.warmup)
+    res, keep = {}, {}
+    for b in (8, 16, 32):
+        for prec, name, dt in ((st.STTSM_BF16X6, "bf16x6", torch.float32), (st.STTSM_FP64, "fp64", torch.float64)):
+            dense = torch.empty(n ** m, dtype=dt, device="cuda")
+            synth.dev_sym_uniform_dense(dense.data_ptr(), m, n, SEED_A, "f64" if dt == torch.float64 else "f32", stream)
+            A = torch.empty(st.bcss_num_elems(m, n, b), dtype=dt, device="cuda")
+            st.bcss_pack(dense, A, m, n, b)
+            del dense
+            Xsrc = Xh if name == "fp64" else X32
+            X = torch.from_numpy(np.asfortranarray(Xsrc).reshape(-1, order="F").copy()).to(device="cuda", dtype=dt)
+            C = torch.empty(st.bcss_num_elems(m, p, b), dtype=dt, device="cuda")
+            ws = st.workspace_tensor(m, n, p, b, prec)
+            st.sttsm_profile_enable(True)
+            st.sttsm_bcss(A, X, m, n, p, b, C, prec, ws)
+            torch.cuda.synchronize()
+            kinds = sorted({r["kind"] for r in st.sttsm_profile_read() if r["kind"] != "split"})
+            st.sttsm_profile_enable(False)
+            tot, per = time_steps(torch, lambda: st.sttsm_bcss(A, X, m, n, p, b, C, prec, ws), steps, warm)
+            F = st.sttsm_flops(m, n, p, b)
+            res["%s_b%d" % (name, b)] = {"tflops": F / (tot / steps * 1e-3) / 1e12, "ms_per_step": tot / steps,
+                                         "p99_ms": float(np.percentile(per, 99)), "level_kernel": kinds}
+            keep[(name, b)] = C.double().cpu().numpy()
+            del A, C, ws, X
+            torch.cuda.empty_cache()
+    oracle.build()
+    A_dense = synth.sym_uniform_dense(m, n, SEED_A)
+    J = np.sort(np.random.default_rng(SEED_J).integers(0, p, size=(64, m)), axis=1)
+    ref = {"bf16x6": oracle.sttsm_entries(A_dense, X32, m, J), "fp64": oracle.sttsm_entries(A_dense, Xh, m, J)}
+    for (name, b), c in keep.items():
+        got = np.array([c[bcss_pos_m(j, b, m)] for j in J])
+        res["%s_b%d" % (name, b)]["rel_err"] = float(np.linalg.norm(got - ref[name]) / np.linalg.norm(ref[name]))
+    best = max((k for k in res if k.startswith("bf16x6")), key=lambda k: res[k]["tflops"])
+    line = {"metric": "sttsm TFLOP/s, m=4 n=128 p=64 (compressing)", "value": res[best]["tflops"], "unit": "TFLOP/s",
+            "n_gpus": 1, "steps": steps, "warmup": warm, "higher_is_better": True, "dtype": "bf16x6",
+            "data": "synthetic", "config": {"workload": "sttsm m=4 n=128 p=64, X orthonormal rows, b in {8,16,32}",
+                                            "best": best, "tolerance": {"bf16x6": 1e-6, "fp64": 1e-12},
+                                            "oracle_samples": 64},
+            "results": res}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_batch(args):
@@ -570,6 +657,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "m4":
+        return run_m4(args)
     import torch
     import torch.distributed as dist
 
@@ -687,7 +776,7 @@ def main():
                            "useful_flops_per_step": F, "l2": "inputs larger than L2 (A in BCSS FP32: %.0f MB)"
                            % (A.numel() * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e, "fp64_path": fp64, "rel_err": rel_err,
-                "gpu_launches": args.steps * (1 + M), "clocks": clk}
+                "gpu_launches": args.steps * (M + (2 if "tma" in kinds else 1)), "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
