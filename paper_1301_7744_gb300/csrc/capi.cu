@@ -443,7 +443,7 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
             for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
             const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
             ProfScope ps(stream, 3, d, lflops);
-            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d == m - 1, stream));
+            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d == m - 1, b == 16, stream));
             if (rc != STTSM_OK) return rc;
         }
         return STTSM_OK;

@@ -50,9 +50,21 @@ struct SmemT {
     static constexpr int BYTES = STAGES * STAGE + 1024 + 256;
 };
 
+// acc[0..63] += 64 consecutive TMEM columns of this warp's lanes from taddr
+__device__ __forceinline__ void tmem_fold64(float* acc, uint32_t taddr)
+{
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float v[8];
+        tmem_ld_32x32b_x8(taddr + c * 8, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
+    }
+}
+
 }  // namespace
 
-template <int NP, bool FP32_OUT>
+template <int NP, bool FP32_OUT, bool B16>
 __global__ void __launch_bounds__(T_THREADS, 1)
 level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restrict__ insts,
                  const Tile* __restrict__ tiles, int ntiles, int* status)
@@ -110,7 +122,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int pr = t.row0 / I.R, rr0 = t.row0 - pr * I.R;
                 const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
                 const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
-                const bool b16 = I.b == 16;
+                constexpr bool b16 = B16;
                 for (int ks = 0; ks < nk; ++ks) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                     const int k0 = ks * TC_KC;
@@ -176,7 +188,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int pr = t.row0 / I.R;
                 const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
                 const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
-                const bool b16 = I.b == 16;
+                constexpr bool b16 = B16;
                 const int nmma = (t.ncols + 15) & ~15;
                 const uint32_t idesc_k = idesc_bf16(nmma), idesc_mn = idesc_bf16_amn(nmma);
                 // B piece planes are as tall as the X box the producer used
@@ -253,30 +265,27 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue (warps 0-15)
+        // warp (quad, cq) owns TMEM lanes 32 quad.. (rows) and the cq-th quarter
+        // of the tile's columns (a multiple of 8, <= 64), so narrow tiles keep
+        // all 16 warps busy.  The fold always reads 64 columns from the warp's
+        // base (inside the accumulator's 256 columns for every quarter size);
+        // columns past the quarter are never stored.
         const int quad = warp & 3, cq = warp >> 2;
         const int row = quad * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-        const int colbase = cq * 64;
         uint32_t group_phase = 0;
         bool ok = true;
         float acc[64];
-        auto fold = [&](uint32_t tm, bool active) {
-            if (active) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    float v[8];
-                    tmem_ld_32x32b_x8(tm + lane_off + colbase + c * 8, v);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
-                }
-            }
-        };
         for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
             const Tile t = tiles[ti];
             const TmaInst& TI = insts ? insts[t.inst] : inst0;
             const LevelInst& I = TI.L;
             const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
             const int ngroups = (nk + T_GS - 1) / T_GS;
+            // (the FP32 writer of C keeps whole 64-column quarters: its rows are
+            // contiguous, and longer runs per thread store faster)
+            const int cw = FP32_OUT ? 64 : ((((t.ncols + 15) & ~15) + 3) / 4 + 7) & ~7;
+            const int colbase = cq * cw;
             const bool active = colbase < t.ncols;
 #pragma unroll
             for (int i = 0; i < 64; ++i) acc[i] = 0.f;
@@ -284,13 +293,13 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 if (!mbar_wait(d0_full, group_phase, abort_flag, status)) { ok = false; break; }
                 group_phase ^= 1u;
                 tc_fence_after();
-                fold(tmem_d0, active);
+                if (active) tmem_fold64(acc, tmem_d0 + lane_off + (uint32_t)colbase);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(d0_empty);
             }
             if (!ok) break;
-            fold(tmem_d1, active);
+            if (active) tmem_fold64(acc, tmem_d1 + lane_off + (uint32_t)colbase);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(d1_empty);
@@ -301,7 +310,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int64_t rowoff = __ldg(I.OFF + I.k * I.R + rr);
                 const int cg0 = t.col0 + colbase;
                 int jb = cg0 / b, c = cg0 - jb * b;
-                const int nvalid = t.ncols - colbase;
+                const int nvalid = min(t.ncols - colbase, cw);
                 if constexpr (FP32_OUT) {
                     float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
                     // the FP32 output is C (k = 0): a row's columns are contiguous within a
@@ -402,38 +411,44 @@ int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, i
     return (int)cudaGetLastError();
 }
 
-int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, bool fp32_out, cudaStream_t s)
+template <int NP, bool F, bool B>
+static int launch_tma_variant(const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles, int grid,
+                              int* d_status, cudaStream_t s)
 {
-    if (ntiles <= 0) return 0;
-    const int grid = ntiles < num_sms ? ntiles : num_sms;
     static std::mutex mu;
-    static bool attr_set[4][64] = {};
+    static bool attr_set[64] = {};
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
-    const int v = (npiece - 2) * 2 + (fp32_out ? 1 : 0);
+    if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorInvalidDevice;
     {
         std::lock_guard<std::mutex> lock(mu);
-        if (dev >= 0 && dev < 64 && !attr_set[v][dev]) {
-            cudaError_t e;
-            switch (v) {
-            case 0: e = cudaFuncSetAttribute(level_tma_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<2>::BYTES); break;
-            case 1: e = cudaFuncSetAttribute(level_tma_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<2>::BYTES); break;
-            case 2: e = cudaFuncSetAttribute(level_tma_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<3>::BYTES); break;
-            default: e = cudaFuncSetAttribute(level_tma_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<3>::BYTES); break;
-            }
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            const cudaError_t e = cudaFuncSetAttribute(level_tma_kernel<NP, F, B>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<NP>::BYTES);
             if (e != cudaSuccess) return (int)e;
-            attr_set[v][dev] = true;
+            attr_set[dev] = true;
         }
     }
-    switch (v) {
-    case 0: level_tma_kernel<2, false><<<grid, T_THREADS, SmemT<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status); break;
-    case 1: level_tma_kernel<2, true><<<grid, T_THREADS, SmemT<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status); break;
-    case 2: level_tma_kernel<3, false><<<grid, T_THREADS, SmemT<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status); break;
-    default: level_tma_kernel<3, true><<<grid, T_THREADS, SmemT<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status); break;
-    }
+    level_tma_kernel<NP, F, B><<<grid, T_THREADS, SmemT<NP>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
     return (int)cudaGetLastError();
+}
+
+int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
+                     int num_sms, int* d_status, bool fp32_out, bool b16, cudaStream_t s)
+{
+    if (ntiles <= 0) return 0;
+    if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    const int v = (npiece - 2) * 4 + (fp32_out ? 2 : 0) + (b16 ? 1 : 0);
+    switch (v) {
+    case 0: return launch_tma_variant<2, false, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    case 1: return launch_tma_variant<2, false, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    case 2: return launch_tma_variant<2, true, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    case 3: return launch_tma_variant<2, true, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    case 4: return launch_tma_variant<3, false, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    case 5: return launch_tma_variant<3, false, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    case 6: return launch_tma_variant<3, true, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    default: return launch_tma_variant<3, true, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    }
 }
 
 }  // namespace sttsm

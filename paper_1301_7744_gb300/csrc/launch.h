@@ -63,8 +63,10 @@ struct TmaInst {
     LevelInst L;
 };
 // fp32_out: the launch writes FP32 (C at the last level) instead of BF16 pieces.
+// b16: every instance of the launch has b = 16 (two 16-wide blocks per stage);
+// otherwise every instance has b a multiple of 32.
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, bool fp32_out, cudaStream_t s);
+                     int num_sms, int* d_status, bool fp32_out, bool b16, cudaStream_t s);
 int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s);
 
 // Tensor maps of a BF16-piece parent array with nblocks stored blocks (all

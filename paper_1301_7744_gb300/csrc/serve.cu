@@ -236,10 +236,12 @@ int launch_step(sttsm_serve_s* H)
     std::vector<SplitDesc> split;
     int64_t split_blocks = 0;
     std::vector<const Req*> asplit;            // TMA requests whose A is split this step
-    // groups: 0 gathered A, 1 small tiles, 2 TMA writing pieces, 3 TMA writing C
+    // groups: 0 gathered A, 1 small tiles, 2 / 3 TMA writing pieces / C with b a
+    // multiple of 32, 4 / 5 the same with b = 16
+    constexpr int NG = 6;
     std::vector<TcInst> insts[2];
-    std::vector<TmaInst> tinsts[2];
-    std::vector<Tile> tiles[4];
+    std::vector<TmaInst> tinsts[NG - 2];
+    std::vector<Tile> tiles[NG];
     std::vector<uint64_t> finishing;
     for (uint64_t tk : H->active) {
         Req& R = H->reqs[tk];
@@ -255,7 +257,7 @@ int launch_step(sttsm_serve_s* H)
             R.split_done = true;
         }
         const bool last = R.level == R.s.m - 1;
-        const int g = R.tma ? (last ? 3 : 2) : (R.small ? 1 : 0);
+        const int g = R.tma ? (last ? 3 : 2) + (R.s.b == 16 ? 2 : 0) : (R.small ? 1 : 0);
         int32_t e;
         if (g < 2) { e = (int32_t)insts[g].size(); insts[g].push_back(R.inst[R.level]); }
         else { e = (int32_t)tinsts[g - 2].size(); tinsts[g - 2].push_back(R.tinst[R.level]); }
@@ -264,11 +266,11 @@ int launch_step(sttsm_serve_s* H)
             tiles[g].push_back(t);
         }
     }
-    // staging layout: [TmaInst 2, 3][TcInst 0, 1][tiles 0..3][split]
-    size_t off = 0, o_ti[2], o_i[2], o_t[4], o_s;
-    for (int k = 0; k < 2; ++k) { o_ti[k] = off; off = up256(off + tinsts[k].size() * sizeof(TmaInst)); }
+    // staging layout: [TmaInst 2..5][TcInst 0, 1][tiles 0..5][split]
+    size_t off = 0, o_ti[NG - 2], o_i[2], o_t[NG], o_s;
+    for (int k = 0; k < NG - 2; ++k) { o_ti[k] = off; off = up256(off + tinsts[k].size() * sizeof(TmaInst)); }
     for (int k = 0; k < 2; ++k) { o_i[k] = off; off = up256(off + insts[k].size() * sizeof(TcInst)); }
-    for (int k = 0; k < 4; ++k) { o_t[k] = off; off = up256(off + tiles[k].size() * sizeof(Tile)); }
+    for (int k = 0; k < NG; ++k) { o_t[k] = off; off = up256(off + tiles[k].size() * sizeof(Tile)); }
     o_s = off;
     off = up256(off + split.size() * sizeof(SplitDesc));
     Staging& S = H->stg[H->cur];
@@ -276,11 +278,11 @@ int launch_step(sttsm_serve_s* H)
     int rc = grow_staging(H, S, off);
     if (rc != STTSM_OK) return rc;
     if (!S.copied && cudaEventCreateWithFlags(&S.copied, cudaEventDisableTiming) != cudaSuccess) return STTSM_ERR_CUDA;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < NG - 2; ++k)
         if (!tinsts[k].empty()) memcpy(S.h + o_ti[k], tinsts[k].data(), tinsts[k].size() * sizeof(TmaInst));
+    for (int k = 0; k < 2; ++k)
         if (!insts[k].empty()) memcpy(S.h + o_i[k], insts[k].data(), insts[k].size() * sizeof(TcInst));
-    }
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < NG; ++k)
         if (!tiles[k].empty()) memcpy(S.h + o_t[k], tiles[k].data(), tiles[k].size() * sizeof(Tile));
     if (!split.empty()) memcpy(S.h + o_s, split.data(), split.size() * sizeof(SplitDesc));
     if (cudaMemcpyAsync(S.d, S.h, off, cudaMemcpyHostToDevice, H->stream) != cudaSuccess) return STTSM_ERR_CUDA;
@@ -295,7 +297,7 @@ int launch_step(sttsm_serve_s* H)
     TcInst dummy;
     memset(&dummy, 0, sizeof(dummy));
     static TmaInst tdummy;   // zero-initialised; unused when a descriptor table is passed
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NG; ++k) {
         if (tiles[k].empty()) continue;
         const Tile* dt = (const Tile*)(S.d + o_t[k]);
         const int n = (int)tiles[k].size();
@@ -303,7 +305,8 @@ int launch_step(sttsm_serve_s* H)
         if (k == 0) lrc = launch_level_tc(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, H->stream);
         else if (k == 1 && small_kernel_kind() == 0) lrc = launch_level_small_f32_tc((const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->stream);
         else if (k == 1) lrc = launch_level_tc_small(H->np, dummy, (const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->status, H->stream);
-        else lrc = launch_level_tma(H->np, tdummy, (const TmaInst*)(S.d + o_ti[k - 2]), dt, n, H->sms, H->status, k == 3, H->stream);
+        else lrc = launch_level_tma(H->np, tdummy, (const TmaInst*)(S.d + o_ti[k - 2]), dt, n, H->sms, H->status,
+                                    (k & 1) == 1, k >= 4, H->stream);
         if (lrc != 0) return STTSM_ERR_CUDA;
     }
     H->cur ^= 1;
