@@ -39,7 +39,16 @@ constexpr int T_THREADS = 576;
 constexpr int T_EPI_WARPS = 16;
 constexpr int T_MMA_WARP = 16;
 constexpr int T_TMA_WARP = 17;
-constexpr int T_GS = 2;
+// D0 (x0*y0) restarts: the first group of a tile spans T_GS0 stages (room for
+// the epilogue to finish the previous tile's stores before the first drain),
+// the later ones T_GS stages
+constexpr int T_GS = 2, T_GS0 = 4;
+__host__ __device__ constexpr bool d0_group_start(int ks) { return ks == 0 || (ks >= T_GS0 && (ks - T_GS0) % T_GS == 0); }
+__host__ __device__ constexpr bool d0_group_end(int ks, int nk)
+{
+    return ks == nk - 1 || ks == T_GS0 - 1 || (ks >= T_GS0 && (ks - T_GS0) % T_GS == T_GS - 1);
+}
+__host__ __device__ constexpr int d0_groups(int nk) { return nk <= T_GS0 ? 1 : 1 + (nk - T_GS0 + T_GS - 1) / T_GS; }
 
 template <int NP>
 struct SmemT {
@@ -239,7 +248,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                             }
                         }
                     }
-                    const bool group_start = (ks % T_GS) == 0;
+                    const bool group_start = d0_group_start(ks);
                     if (group_start) {
                         if (!mbar_wait(d0_empty, group_phase ^ 1u, abort_flag, status)) { ok = false; break; }
                         group_phase ^= 1u;
@@ -251,7 +260,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                             tc_mma(tmem_d0, adesc(0, kh), smem_desc_sw64(sB + kh * 32), mnk[kh] ? idesc_mn : idesc_k,
                                    (group_start && kh == 0) ? 0u : 1u);
                     tc_commit(empty_bar(stage));
-                    if ((ks % T_GS) == T_GS - 1 || ks == nk - 1) tc_commit(d0_full);
+                    if (d0_group_end(ks, nk)) tc_commit(d0_full);
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -281,7 +290,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             const TmaInst& TI = insts ? insts[t.inst] : inst0;
             const LevelInst& I = TI.L;
             const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
-            const int ngroups = (nk + T_GS - 1) / T_GS;
+            const int ngroups = d0_groups(nk);
             // (the FP32 writer of C keeps whole 64-column quarters: its rows are
             // contiguous, and longer runs per thread store faster)
             const int cw = FP32_OUT ? 64 : ((((t.ncols + 15) & ~15) + 3) / 4 + 7) & ~7;
