@@ -259,9 +259,10 @@ def time_steps(torch, fn, steps, warmup, per_step_events=True):
 
 
 def profiled_traffic(b, prec, kinds):
-    """DRAM bytes (read + write) per step of the level kernel, summed over the m level
-    launches, from the committed ncu summary of this workload (profiles/traffic.json),
-    or None when no capture of the current kernel for this block size exists."""
+    """DRAM bytes (read + write) per launch of the level kernel (mean of the m level
+    launches of a step), from the committed ncu summary of this workload
+    (profiles/traffic.json), or None when no capture of the current kernel for this
+    block size exists."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -270,7 +271,7 @@ def profiled_traffic(b, prec, kinds):
         return None
     key = "%s_b%d_%s" % (kinds[0] if kinds else "", b, prec)
     v = d.get(key)
-    return v.get("dram_bytes_per_step") if isinstance(v, dict) else None
+    return v.get("dram_bytes_per_launch") if isinstance(v, dict) else None
 
 
 def end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, steps):
@@ -745,8 +746,20 @@ def main():
                        "mma_frac_of_peak": v["flops"] * nprod / (v["ms"] * 1e-3) / 1e12 / peak}
               for k, v in sorted(per_level.items())}
     traffic = profiled_traffic(b, args.prec, kinds)
+    # algorithmic bytes per level launch (mean): parent BF16 pieces read + output written
+    # (pieces, or FP32 C at the last level), from the level sizes
+    alg = 0.0
+    npc = 3 if prec == st.STTSM_BF16X6 else 2
+    for d in range(M):
+        _, _, info = st.sttsm_plan_level(M, N, P, b, prec, d)
+        par = info["nodes_parent"] * info["P_parent"] * info["bm"] * npc * 2
+        out = info["nodes_out"] * info["P_out"] * info["bm"] * (4 if d == M - 1 else npc * 2)
+        alg += par + out
+    alg_bytes = alg / M
     roofline = {"bound": "tensor", "achieved": mma_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": mma_tflops / peak, "traffic": traffic,
+                "traffic_per": "launch (DRAM read + write, mean of the m level launches of a step; ncu)",
+                "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": {"tma": "level_tma_kernel", "tc": "level_tc_kernel"}[kinds[0]] + " (all m levels)" if kinds else None,
                 "achieved_counts": "useful flops x %d piece products per launch / CUDA-event duration" % nprod,
                 "peak_source": "bf16_tflops_sustained of %s MEASURED_PEAKS" % pk_src,
