@@ -52,9 +52,10 @@ def parse_args():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
-    ap.add_argument("--workload", default="single", choices=["single", "m4", "batch", "serve"],
+    ap.add_argument("--workload", default="single", choices=["single", "m4", "abo", "batch", "serve"],
                     help="single: m=3 n=p=768 instance (default); m4: m=4 n=128 p=64 compressing instance; "
-                         "batch: 4096 mixed instances; serve: Poisson stream")
+                         "abo: all modes but one on the m=3 n=p=768 instance; batch: 4096 mixed instances; "
+                         "serve: Poisson stream")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--ws-gb", type=float, default=48.0, help="batch workspace budget (GiB)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -423,6 +424,58 @@ def run_m4(args):
     return 0
 
 
+def run_abo(args):
+    """Multiplication in all modes but one, B = A x_1 X x_2 X on the m = 3, n = p = 768
+    instance (b = 64, BF16X6): TFLOP/s of levels 0 .. m-2 and the error of a 4 x 4 x 4
+    grid of sampled entries against the FP64 oracle's chain restricted to those rows."""
+    import math
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_7744_gb300 as st
+    import synth
+    import oracle
+    b = 64 if args.b == "auto" else int(args.b)
+    prec = st.STTSM_BF16X6 if args.prec == "bf16x6" else st.STTSM_BF16X3
+    Xh = synth.x_gaussian(SEED_X, P, N)
+    X32 = Xh.astype(np.float32).astype(np.float64)
+    dX = torch.from_numpy(xcol32(Xh)).cuda()
+    A = make_device_inputs(st, torch, b, torch.float32)
+    T = torch.empty(st.sttsm_all_but_one_elems(M, N, P, b), dtype=torch.float32, device="cuda")
+    ws = st.workspace_tensor(M, N, P, b, prec)
+    F = st.sttsm_all_but_one_flops(M, N, P, b)
+    steps, warm = max(3, min(args.steps, 100)), max(3, args.warmup)
+    clocks = ClockSampler()
+    clocks.start()
+    tot, per = time_steps(torch, lambda: st.sttsm_bcss_all_but_one(A, dX, M, N, P, b, T, prec, ws), steps, warm)
+    clk = clocks.stop()
+    ms = tot / steps
+    rng = np.random.default_rng(SEED_J)
+    ri, rj = np.sort(rng.integers(0, N, size=4)), np.sort(rng.integers(0, P, size=4))
+    oracle.build()
+    A_dense = synth.sym_uniform_dense(M, N, SEED_A)
+    ref = oracle.ttm_chain(A_dense, [np.eye(N)[ri], X32[rj], X32[rj]], M).reshape(4, 4, 4, order="F")
+    t = T.double().cpu().numpy()
+    nbar = -(-N // b)
+    got = np.empty_like(ref)
+    for a, i in enumerate(ri):
+        for c1, j1 in enumerate(rj):
+            for c2, j2 in enumerate(rj):
+                lo, hi = sorted((int(j1), int(j2)), key=lambda v: v // b)
+                node = math.comb(lo // b + 0, 1) + math.comb(hi // b + 1, 2)
+                off = int(i) % b + (lo % b) * b + (hi % b) * b * b
+                got[a, c1, c2] = t[(node * nbar + int(i) // b) * b ** M + off]
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    line = {"metric": "sttsm all-but-one TFLOP/s (A x_1 X x_2 X, Tbl. 4 count of levels 0..m-2)", "value": F / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": ms,
+            "p99_ms_per_step": float(np.percentile(per, 99)), "higher_is_better": True, "dtype": args.prec,
+            "data": "synthetic", "config": {"workload": "all modes but one, m=3 n=p=768 b=%d %s" % (b, args.prec.upper()),
+                                            "useful_flops_per_step": F},
+            "rel_err": {"samples": 64, args.prec: err, "tolerance": 1e-6}, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     """Batched workload: count instances, m in {3,4,5} (weights .5/.3/.2), n in U{8..64},
     p in U{8..n}, b per instance by sttsm_autotune_b over {4, 8, 16}; BF16X6; one
@@ -660,6 +713,8 @@ def main():
         return run_batch(args)
     if args.workload == "m4":
         return run_m4(args)
+    if args.workload == "abo":
+        return run_abo(args)
     import torch
     import torch.distributed as dist
 

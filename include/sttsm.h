@@ -129,6 +129,32 @@ int sttsm_workspace_size(int m, int64_t n, int64_t p, int b, int prec, size_t* b
 int sttsm_bcss(const void* A_bcss, const void* X, int m, int64_t n, int64_t p, int b,
                void* C_bcss, int prec, void* workspace, size_t ws_bytes, void* stream);
 
+/* Multiplication in all modes but one, the related operation Sec. 2.5 names:
+ * B := A x_1 X x_2 ... x_{m-1} X with mode 0 left untransformed, so B is
+ * n x p x ... x p and symmetric in its last m-1 modes (Sec. 2.3).  B is the
+ * temporary T^(1) of the algorithm-by-blocks (levels 0 .. m-2 of Fig. 5 with
+ * Thm. 1), returned in its partially symmetric block storage:
+ *   T: sttsm_all_but_one_elems(m, n, p, b) elements (FP64 for STTSM_FP64,
+ *      else FP32), laid out [node][ib][b^m]:
+ *        node = colex rank of the sorted block tuple (jb_1 <= ... <= jb_{m-1})
+ *               of the transformed modes, C(pbar+m-2, m-1) nodes;
+ *        ib   = block index of mode 0, nbar blocks per node;
+ *        in-block offset i_0 + sum_{t=1}^{m-1} j_t b^t (local indices; mode t
+ *               holds the t-th smallest block index of the tuple).
+ *      Entries past n (mode 0) or p (modes 1..m-1) are zero.
+ *   A_bcss, X, prec, workspace (>= sttsm_workspace_size(m, n, p, b, prec)
+ *   bytes) and errors as sttsm_bcss.  2 <= m <= 8 (STTSM_ERR_ARG otherwise). */
+int sttsm_bcss_all_but_one(const void* A_bcss, const void* X, int m, int64_t n, int64_t p, int b,
+                           void* T, int prec, void* workspace, size_t ws_bytes, void* stream);
+
+/* Elements of the all-but-one result: C(pbar+m-2, m-1) * nbar * b^m; -1 on
+ * invalid arguments (m < 2). */
+int64_t sttsm_all_but_one_elems(int m, int64_t n, int64_t p, int b);
+
+/* Useful flops of the all-but-one result: the Tbl. 4 sum of sttsm_flops over
+ * levels d = 0 .. m-2 only. */
+double sttsm_all_but_one_flops(int m, int64_t n, int64_t p, int b);
+
 /* End-to-end variant on HOST buffers: copies A_bcss and X (host, ideally
  * pinned) to the device buffers dA and dX, runs sttsm_bcss, copies C back
  * to the host buffer C_bcss, all enqueued on `stream` (synchronise the

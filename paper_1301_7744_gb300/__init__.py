@@ -79,6 +79,12 @@ def _load():
     L.sttsm_bcss.restype = i32
     L.sttsm_bcss_host.argtypes = [P, P, i32, i64, i64, i32, P, i32, P, P, P, P, ctypes.c_size_t, P]
     L.sttsm_bcss_host.restype = i32
+    L.sttsm_bcss_all_but_one.argtypes = [P, P, i32, i64, i64, i32, P, i32, P, ctypes.c_size_t, P]
+    L.sttsm_bcss_all_but_one.restype = i32
+    L.sttsm_all_but_one_elems.argtypes = [i32, i64, i64, i32]
+    L.sttsm_all_but_one_elems.restype = i64
+    L.sttsm_all_but_one_flops.argtypes = [i32, i64, i64, i32]
+    L.sttsm_all_but_one_flops.restype = ctypes.c_double
     L.sttsm_device_status.argtypes = []
     L.sttsm_device_status.restype = i32
     L.sttsm_autotune_b.argtypes = [i32, i64, i64, i32, P, i32]
@@ -237,6 +243,31 @@ def sttsm_bcss(A, X, m: int, n: int, p: int, b: int, C, prec: int, workspace, st
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("sttsm_bcss", _load().sttsm_bcss(_dptr(A), _dptr(X), m, n, p, b, _dptr(C), prec, ws, nbytes,
                                             _stream(stream)))
+
+
+def sttsm_all_but_one_elems(m: int, n: int, p: int, b: int) -> int:
+    return int(_load().sttsm_all_but_one_elems(m, n, p, b))
+
+
+def sttsm_all_but_one_flops(m: int, n: int, p: int, b: int) -> float:
+    return float(_load().sttsm_all_but_one_flops(m, n, p, b))
+
+
+def sttsm_bcss_all_but_one(A, X, m: int, n: int, p: int, b: int, T, prec: int, workspace, stream=None) -> None:
+    """T := A x_1 X ... x_{m-1} X (mode 0 untransformed) in the partially symmetric
+    block storage [node][ib][b^m] of the header; T holds sttsm_all_but_one_elems
+    elements.  X: p*n elements, column-major."""
+    import torch
+    want = torch.float64 if prec == STTSM_FP64 else torch.float32
+    for name, t in (("A", A), ("X", X), ("T", T)):
+        if t.dtype != want:
+            raise ValueError("%s must be %s for precision %s" % (name, want, PREC_NAMES.get(prec, prec)))
+    if A.numel() != bcss_num_elems(m, n, b) or X.numel() != p * n or T.numel() != sttsm_all_but_one_elems(m, n, p, b):
+        raise ValueError("size mismatch")
+    ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None and workspace.numel() else ctypes.c_void_p(0)
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("sttsm_bcss_all_but_one",
+           _load().sttsm_bcss_all_but_one(_dptr(A), _dptr(X), m, n, p, b, _dptr(T), prec, ws, nbytes, _stream(stream)))
 
 
 def sttsm_bcss_noalloc(A, X, m: int, n: int, p: int, b: int, C, prec: int, stream=None) -> None:

@@ -379,8 +379,16 @@ int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_
     return STTSM_OK;
 }
 
-int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b, void* C, int prec,
-               void* workspace, size_t ws_bytes, void* stream_)
+}  // extern "C"
+
+namespace sttsm {
+namespace {
+
+// Levels 0 .. nlev-1 of the chain (nlev = m: C; nlev = m - 1: the all-but-one
+// result T^(1)); the last of them writes `C` (FP32 / FP64), the others the
+// workspace's ping-pong buffers.
+int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, void* C, int prec,
+              void* workspace, size_t ws_bytes, void* stream_, int nlev)
 {
     if (!A || !X || !C) return STTSM_ERR_ARG;
     if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
@@ -419,15 +427,15 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
         for (int xs = 0; xs < 3 && rc == STTSM_OK; ++xs)
             rc = make_x_tensor_map(&tm.tmX[xs], ws + w.xpieces, np, w.rows, w.Kp, TC_BN >> xs);
         if (rc != STTSM_OK) return rc;
-        for (int d = 0; d < m; ++d) {
+        for (int d = 0; d < nlev; ++d) {
             const LevelShape& LS = s.lv[d];
             const void* parent = d == 0 ? (const void*)(ws + w.apieces) : bufs[(d - 1) & 1];
             rc = make_a_tensor_maps(tm.tmA, parent, LS.nodes_parent * LS.P_parent, np, b, m, LS.k);
             if (rc != STTSM_OK) return rc;
             LevelInst& L = tm.L;
             L.parent = parent;
-            L.out = d == m - 1 ? C : bufs[d & 1];
-            L.out_np = d == m - 1 ? 0 : np;
+            L.out = d == nlev - 1 ? C : bufs[d & 1];
+            L.out_np = d == nlev - 1 ? 0 : np;
             L.G = P->d_G[d];
             L.OFF = P->d_G[d] + level_G_size(s, d);
             L.X = X;
@@ -443,7 +451,7 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
             for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
             const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
             ProfScope ps(stream, 3, d, lflops);
-            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d == m - 1, b == 16, stream));
+            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d < nlev - 1 ? TMA_OUT_PIECES : (d == m - 1 ? TMA_OUT_C : TMA_OUT_F32), b == 16, stream));
             if (rc != STTSM_OK) return rc;
         }
         return STTSM_OK;
@@ -459,11 +467,11 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
         rc = make_x_tensor_map(&ti.tmX, ws + w.xpieces, np, w.rows, w.Kp, BN);
         if (rc != STTSM_OK) return rc;
     }
-    for (int d = 0; d < m; ++d) {
+    for (int d = 0; d < nlev; ++d) {
         const LevelShape& LS = s.lv[d];
         LevelInst& L = ti.L;
         L.parent = d == 0 ? A : bufs[(d - 1) & 1];
-        L.out = d == m - 1 ? C : bufs[d & 1];
+        L.out = d == nlev - 1 ? C : bufs[d & 1];
         L.G = P->d_G[d];
         L.OFF = P->d_G[d] + level_G_size(s, d);
         L.X = X;
@@ -486,6 +494,58 @@ int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b,
         if (rc != STTSM_OK) return rc;
     }
     return STTSM_OK;
+}
+
+}  // namespace
+}  // namespace sttsm
+
+extern "C" {
+
+int sttsm_bcss(const void* A, const void* X, int m, int64_t n, int64_t p, int b, void* C, int prec,
+               void* workspace, size_t ws_bytes, void* stream)
+{
+    return sttsm::run_chain(A, X, m, n, p, b, C, prec, workspace, ws_bytes, stream, m);
+}
+
+int sttsm_bcss_all_but_one(const void* A, const void* X, int m, int64_t n, int64_t p, int b, void* T, int prec,
+                           void* workspace, size_t ws_bytes, void* stream)
+{
+    if (m < 2) return STTSM_ERR_ARG;
+    return sttsm::run_chain(A, X, m, n, p, b, T, prec, workspace, ws_bytes, stream, m - 1);
+}
+
+int64_t sttsm_all_but_one_elems(int m, int64_t n, int64_t p, int b)
+{
+    if (m < 2 || m > STTSM_MAX_M || n < 1 || p < 1 || b < 1) return -1;
+    const int64_t nbar = (n + b - 1) / b, pbar = (p + b - 1) / b;
+    // C(pbar + m - 2, m - 1) sorted (m-1)-tuples of p-blocks, nbar blocks each
+    double c = 1.0;
+    for (int i = 1; i <= m - 1; ++i) c = c * (double)(pbar - 1 + i) / i;
+    double e = c * (double)nbar;
+    for (int a = 0; a < m; ++a) e *= b;
+    if (e > 9.0e18) return -1;
+    int64_t r = 1;
+    for (int i = 1; i <= m - 1; ++i) r = r * (pbar - 1 + i) / i;
+    r *= nbar;
+    for (int a = 0; a < m; ++a) r *= b;
+    return r;
+}
+
+double sttsm_all_but_one_flops(int m, int64_t n, int64_t p, int b)
+{
+    if (m < 2 || n < 1 || p < 1 || b < 1) return -1.0;
+    const double nbar = (double)((n + b - 1) / b), pbar = (double)((p + b - 1) / b);
+    auto C = [](double x, int y) {
+        if (y < 0 || x < y) return 0.0;
+        double c = 1.0;
+        for (int i = 1; i <= y; ++i) c = c * (x - y + i) / i;
+        return c;
+    };
+    double s = 0.0;
+    for (int d = 0; d < m - 1; ++d) s += C(pbar + d, d + 1) * C(nbar + m - d - 2, m - d - 1);
+    double bp = 1.0;
+    for (int a = 0; a <= m; ++a) bp *= b;
+    return 2.0 * nbar * bp * s;
 }
 
 int sttsm_bcss_host(const void* A, const void* X, int m, int64_t n, int64_t p, int b, void* C, int prec,

@@ -73,7 +73,7 @@ __device__ __forceinline__ void tmem_fold64(float* acc, uint32_t taddr)
 
 }  // namespace
 
-template <int NP, bool FP32_OUT, bool B16>
+template <int NP, int OUT, bool B16>
 __global__ void __launch_bounds__(T_THREADS, 1)
 level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restrict__ insts,
                  const Tile* __restrict__ tiles, int ntiles, int* status)
@@ -293,7 +293,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             const int ngroups = d0_groups(nk);
             // (the FP32 writer of C keeps whole 64-column quarters: its rows are
             // contiguous, and longer runs per thread store faster)
-            const int cw = FP32_OUT ? 64 : ((((t.ncols + 15) & ~15) + 3) / 4 + 7) & ~7;
+            const int cw = OUT == TMA_OUT_C ? 64 : ((((t.ncols + 15) & ~15) + 3) / 4 + 7) & ~7;
             const int colbase = cq * cw;
             const bool active = colbase < t.ncols;
 #pragma unroll
@@ -320,7 +320,16 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int cg0 = t.col0 + colbase;
                 int jb = cg0 / b, c = cg0 - jb * b;
                 const int nvalid = min(t.ncols - colbase, cw);
-                if constexpr (FP32_OUT) {
+                if constexpr (OUT == TMA_OUT_F32) {
+                    // FP32 output of a level k >= 1 (the all-but-one result): the columns
+                    // of a row are b^k apart inside a child's block
+                    float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) {
+                        if (e < nvalid) dst[(int64_t)bk * c] = acc[e];
+                        if (++c == b) { c = 0; dst += I.P_out * I.bm; }
+                    }
+                } else if constexpr (OUT == TMA_OUT_C) {
                     float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
                     // the FP32 output is C (k = 0): a row's columns are contiguous within a
                     // child's block, and b (a multiple of 32) keeps groups of 4 inside blocks
@@ -420,7 +429,7 @@ int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, i
     return (int)cudaGetLastError();
 }
 
-template <int NP, bool F, bool B>
+template <int NP, int OUT, bool B>
 static int launch_tma_variant(const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles, int grid,
                               int* d_status, cudaStream_t s)
 {
@@ -431,32 +440,42 @@ static int launch_tma_variant(const TmaInst& inst0, const TmaInst* d_insts, cons
     {
         std::lock_guard<std::mutex> lock(mu);
         if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-            const cudaError_t e = cudaFuncSetAttribute(level_tma_kernel<NP, F, B>,
+            const cudaError_t e = cudaFuncSetAttribute(level_tma_kernel<NP, OUT, B>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<NP>::BYTES);
             if (e != cudaSuccess) return (int)e;
             attr_set[dev] = true;
         }
     }
-    level_tma_kernel<NP, F, B><<<grid, T_THREADS, SmemT<NP>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
+    level_tma_kernel<NP, OUT, B><<<grid, T_THREADS, SmemT<NP>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
     return (int)cudaGetLastError();
 }
 
+template <int NP, int OUT>
+static int launch_tma_b(bool b16, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
+                        int grid, int* d_status, cudaStream_t s)
+{
+    return b16 ? launch_tma_variant<NP, OUT, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s)
+               : launch_tma_variant<NP, OUT, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+}
+
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, bool fp32_out, bool b16, cudaStream_t s)
+                     int num_sms, int* d_status, int out_kind, bool b16, cudaStream_t s)
 {
     if (ntiles <= 0) return 0;
     if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
+    if (out_kind < TMA_OUT_PIECES || out_kind > TMA_OUT_F32) return (int)cudaErrorInvalidValue;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
-    const int v = (npiece - 2) * 4 + (fp32_out ? 2 : 0) + (b16 ? 1 : 0);
-    switch (v) {
-    case 0: return launch_tma_variant<2, false, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    case 1: return launch_tma_variant<2, false, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    case 2: return launch_tma_variant<2, true, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    case 3: return launch_tma_variant<2, true, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    case 4: return launch_tma_variant<3, false, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    case 5: return launch_tma_variant<3, false, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    case 6: return launch_tma_variant<3, true, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    default: return launch_tma_variant<3, true, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    if (npiece == 2) {
+        switch (out_kind) {
+        case TMA_OUT_PIECES: return launch_tma_b<2, TMA_OUT_PIECES>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+        case TMA_OUT_C: return launch_tma_b<2, TMA_OUT_C>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+        default: return launch_tma_b<2, TMA_OUT_F32>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+        }
+    }
+    switch (out_kind) {
+    case TMA_OUT_PIECES: return launch_tma_b<3, TMA_OUT_PIECES>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    case TMA_OUT_C: return launch_tma_b<3, TMA_OUT_C>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    default: return launch_tma_b<3, TMA_OUT_F32>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
     }
 }
 

@@ -62,11 +62,14 @@ struct TmaInst {
     CUtensorMap tmA[STTSM_MAX_M];
     LevelInst L;
 };
-// fp32_out: the launch writes FP32 (C at the last level) instead of BF16 pieces.
+// out_kind: TMA_OUT_PIECES writes the next level's operand as BF16 pieces,
+// TMA_OUT_C writes FP32 C (the last level, k = 0: a row's columns contiguous),
+// TMA_OUT_F32 writes FP32 at a level k >= 1 (the all-but-one result).
 // b16: every instance of the launch has b = 16 (two 16-wide blocks per stage);
 // otherwise every instance has b a multiple of 32.
+constexpr int TMA_OUT_PIECES = 0, TMA_OUT_C = 1, TMA_OUT_F32 = 2;
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, bool fp32_out, bool b16, cudaStream_t s);
+                     int num_sms, int* d_status, int out_kind, bool b16, cudaStream_t s);
 int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s);
 
 // Tensor maps of a BF16-piece parent array with nblocks stored blocks (all

@@ -59,3 +59,34 @@ def inputs(m, n, p, seed_a=0, seed_x=1, fp32=False):
     if fp32:
         X = X.astype(np.float32).astype(np.float64)
     return A, X
+
+
+def colex_tuples(length, nb):
+    """Sorted block tuples (t_0 <= ... <= t_{length-1}) over [0, nb) in colex order
+    (last index most significant), enumerated directly."""
+    import itertools
+    tups = list(itertools.combinations_with_replacement(range(nb), length))
+    return sorted(tups, key=lambda t: tuple(reversed(t)))
+
+
+def all_but_one_storage(B, m, n, p, b):
+    """The dense all-but-one result B (n x p x ... x p, symmetric in modes 1..m-1)
+    laid out as the library's partially symmetric storage [node][ib][b^m]: node =
+    colex rank of the sorted p-block tuple of modes 1..m-1, ib = block of mode 0,
+    in-block offset i_0 + sum_t j_t b^t; zero past n or p."""
+    nbar, pbar = -(-n // b), -(-p // b)
+    nodes = colex_tuples(m - 1, pbar)
+    out = np.zeros((len(nodes), nbar, b ** m))
+    off = np.arange(b ** m)
+    loc = np.array([(off // b ** t) % b for t in range(m)])   # local index of mode t at in-block offset e
+    for r, tup in enumerate(nodes):
+        for ib in range(nbar):
+            idx = [ib * b + loc[0]] + [tup[t - 1] * b + loc[t] for t in range(1, m)]
+            ok = (idx[0] < n)
+            for t in range(1, m):
+                ok &= idx[t] < p
+            vals = np.zeros(b ** m)
+            sel = np.nonzero(ok)[0]
+            vals[sel] = B[tuple(ix[sel] for ix in idx)]
+            out[r, ib] = vals
+    return out.reshape(-1)

@@ -23,12 +23,13 @@ def st():
     return pkg
 
 
-def emulate(st, m, n, p, b, prec, A_bcss, X):
+def emulate(st, m, n, p, b, prec, A_bcss, X, nlev=None):
+    """Runs levels 0 .. nlev-1 (default all m) and returns the last level's output."""
     nbar, pbar = -(-n // b), -(-p // b)
     Xpad = np.zeros((pbar * b, nbar * b))
     Xpad[:p, :n] = X
     parent = A_bcss
-    for d in range(m):
+    for d in range(m if nlev is None else nlev):
         tiles, G, info = st.sttsm_plan_level(m, n, p, b, prec, d)
         k, R, bm = info["k"], info["R"], info["bm"]
         P_par, P_out, rows_pp, BM = info["P_parent"], info["P_out"], info["rows_per_parent"], info["BM"]
