@@ -241,6 +241,22 @@ def bcss_flops_host(b):
 
 # ---------------------------------------------------------------- our arm
 
+def max_over_ranks(total_ms, device):
+    """The slowest rank's timed-region duration (all ranks call it; needs an
+    initialised process group: NCCL on the GPU, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(flops_per_rank_step, world, total_ms, steps):
+    """Whole-job TFLOP/s: every rank ran `steps` steps of `flops_per_rank_step`
+    useful flops (replicas: weak scaling) in the slowest rank's `total_ms`."""
+    return flops_per_rank_step * world * steps / (total_ms * 1e-3) / 1e12
+
+
 def time_steps(torch, fn, steps, warmup, per_step_events=True):
     for _ in range(warmup):
         fn()
@@ -773,12 +789,10 @@ def main():
     st.sttsm_profile_enable(False)
     clk = clocks.stop()
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
         dist.barrier()
     ms = total_ms / args.steps
-    value = F * world / (ms * 1e-3) / 1e12
+    value = job_rate(F, world, total_ms, args.steps)
 
     # ---- dominant kernel roofline from the library's per-launch events
     recs = st.sttsm_profile_read()
