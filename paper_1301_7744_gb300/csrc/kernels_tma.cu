@@ -340,20 +340,35 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                         if (c == b) { c = 0; dst += I.P_out * I.bm; }
                     }
                 } else {
-                    // BF16 pieces of the next level's operand: [node][block][piece][b^m]
-                    __nv_bfloat16* dst = (__nv_bfloat16*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * NP * I.bm + rowoff;
+                    // BF16 pieces of the next level's operand: [node][block][piece][b^m].
+                    // Columns go in pairs (b is a multiple of 16 and a quarter starts on
+                    // a multiple of 8, so a pair never straddles two children): one
+                    // paired conversion per piece, one running pointer per row.
+                    const int64_t bm = I.bm;
+                    const int64_t child_step = (int64_t)I.P_out * NP * bm;
+                    __nv_bfloat16* dst = (__nv_bfloat16*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * NP * bm +
+                                         rowoff + (int64_t)bk * c;
 #pragma unroll
-                    for (int e = 0; e < 64; ++e) {
+                    for (int e = 0; e < 64; e += 2) {
                         if (e < nvalid) {
-                            float x = acc[e];
+                            float2 x = make_float2(acc[e], acc[e + 1]);
 #pragma unroll
                             for (int pc = 0; pc < NP; ++pc) {
-                                const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                                dst[(int64_t)pc * I.bm + (int64_t)bk * c] = h;
-                                x -= __bfloat162float(h);
+                                const __nv_bfloat162 h = __float22bfloat162_rn(x);
+                                dst[pc * bm] = h.x;
+                                dst[pc * bm + bk] = h.y;
+                                const float2 f = __bfloat1622float2(h);
+                                x.x -= f.x;
+                                x.y -= f.y;
                             }
                         }
-                        if (++c == b) { c = 0; dst += I.P_out * NP * I.bm; }
+                        c += 2;
+                        if (c == b) {
+                            c = 0;
+                            dst += child_step - (int64_t)bk * (b - 2);
+                        } else {
+                            dst += 2 * (int64_t)bk;
+                        }
                     }
                 }
             }
