@@ -16,10 +16,11 @@
 // of tensor map and operand major-ness per stage instead of a data movement.
 //
 // CTA = 18 warps, one per SM, persistent over the tile list:
-//   warps 0-15  epilogue: D0 partials (x0*y0, restarted every 64 contraction
-//               indices) folded into FP32 registers, D1 (cross products) added at
-//               the end of the tile; the row is written as BF16 pieces for the
-//               next level (or FP32 into C at the last level);
+//   warps 0-15  epilogue: D0 partials (x0*y0, restarted after the first 128
+//               contraction indices of a tile and then every 64) folded into FP32
+//               registers, D1 (cross products) added at the end of the tile; the
+//               row is written as BF16 pieces for the next level, FP32 into C at
+//               the last level, or FP32 at level m-2 for the all-but-one result;
 //   warp 16     TMEM allocation and the MMA-issuing thread;
 //   warp 17     the TMA-issuing thread (A box per stage by q, X pieces box).
 #include <cuda_bf16.h>
