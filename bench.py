@@ -602,6 +602,20 @@ def run_batch(args):
             st.sttsm_bcss(A64, X64, m, n, p, b, C64, st.STTSM_FP64, w64)
 
     tot64, _ = time_steps(torch, loop64, 1, 1)
+    # executed FMAs of the small-contraction kernel (tile rows x compile-time column
+    # width x contraction padded to 4) and the algorithmic bytes (parents read, outputs
+    # written, FP32) of every level of every instance, from the library's own plans
+    exec_flops, alg_bytes = 0.0, 0.0
+    for (_, _, _, m, n, p, b) in insts:
+        Kc = ((-(-n // b)) * b + 3) // 4 * 4
+        for d in range(m):
+            tiles, _, li = st.sttsm_plan_level(m, n, p, b, prec, d)
+            w = np.select([tiles[:, 5] <= 8, tiles[:, 5] <= 16, tiles[:, 5] <= 24, tiles[:, 5] <= 32, tiles[:, 5] <= 48],
+                          [8, 16, 24, 32, 48], 64)
+            exec_flops += 2.0 * 128 * Kc * float(w.sum())
+            alg_bytes += 4.0 * (li["nodes_parent"] * li["P_parent"] + li["nodes_out"] * li["P_out"]) * li["bm"]
+    pk, pk_src = peaks()
+    fp32_peak = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     line = {"metric": "sttsm batch TFLOP/s (paper's BCSS flop count), BF16X6, one graph replay per step",
             "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup),
             "ms_per_step": ms, "p99_ms_per_step": float(np.percentile(per, 99)), "higher_is_better": True,
@@ -614,6 +628,17 @@ def run_batch(args):
             "fp64_per_instance_loop": {"value": F / (tot64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms": tot64,
                                        "speedup_of_batch": tot64 / ms},
             "small_kernel": "fp32 cuda-core (n̄b <= 64 contractions)",
+            "median_ms_per_step": float(np.median(per)),
+            "roofline": {"bound": "alu", "achieved": exec_flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": exec_flops / (ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
+                         "kernel": "level_small_f32_kernel (all levels of all instances)",
+                         "achieved_counts": "executed FP32 FMAs x 2 (tile rows x compile-time column width x "
+                                            "contraction padded to 4) per step / step time",
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x sm_max_mhz of %s MEASURED_PEAKS" % pk_src,
+                         "useful_over_executed": F / exec_flops if exec_flops else None},
+            "hbm": {"algorithmic_bytes_per_step": alg_bytes, "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+                    "peak_gbs": float(pk.get("hbm_gbs", 6800.0)),
+                    "counts": "FP32 parents read + outputs written, every level of every instance"},
             "tcgen05_small_tile_kernel": {"value": F / (tot_tc / 3 * 1e-3) / 1e12, "unit": "TFLOP/s",
                                           "ms_per_step": tot_tc / 3} if tot_tc else None,
             "rel_err": {"instances_checked": len(errs), "max": max(errs), "median": float(np.median(errs)),
@@ -868,6 +893,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "p99_ms_per_step": float(np.percentile(per, 99)),
+                "median_ms_per_step": float(np.median(per)),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
                 "data": "synthetic",
                 "config": {"workload": "sttsm m=3 n=p=768 b=%d %s" % (b, args.prec.upper()), "m": M, "n": N, "p": P,
