@@ -271,6 +271,14 @@ int sttsm_set_small_kernel(int kind);
  * failure (1 = bounded wait timed out).  Reading clears it. */
 int sttsm_device_status(void);
 
+/* Self-test of the failure path: launches one kernel whose thread waits on an
+ * mbarrier nothing arrives on, through the same bounded wait the level
+ * kernels use but limited to limit_ms (0 < limit_ms <= 1000); the wait runs
+ * out, the kernel raises the status word and leaves, and the call returns
+ * STTSM_ERR_TIMEOUT with the status cleared (the context stays usable).
+ * Synchronises the device.  STTSM_ERR_ARG for an out-of-range limit. */
+int sttsm_selftest_wait_timeout(double limit_ms);
+
 /* ------------------------------------------------------------------ diagnostics (host) */
 
 /* The plan sttsm_bcss runs at level d (0 <= d < m; level d reads T^(m-d) and

@@ -87,6 +87,8 @@ def _load():
     L.sttsm_all_but_one_flops.restype = ctypes.c_double
     L.sttsm_device_status.argtypes = []
     L.sttsm_device_status.restype = i32
+    L.sttsm_selftest_wait_timeout.argtypes = [ctypes.c_double]
+    L.sttsm_selftest_wait_timeout.restype = i32
     L.sttsm_autotune_b.argtypes = [i32, i64, i64, i32, P, i32]
     L.sttsm_autotune_b.restype = i32
     L.sttsm_batch_plan_create.argtypes = [P, i32, i32, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]
@@ -403,6 +405,11 @@ SMALL_TCGEN05 = 1
 def sttsm_set_small_kernel(kind: int) -> None:
     """Kernel for contractions n̄ b <= 64 under split precisions: SMALL_F32 (default) or SMALL_TCGEN05."""
     _check("sttsm_set_small_kernel", _load().sttsm_set_small_kernel(kind))
+
+
+def sttsm_selftest_wait_timeout(limit_ms: float) -> int:
+    """Runs the bounded-wait self-test; returns the status code (STTSM_ERR_TIMEOUT expected)."""
+    return int(_load().sttsm_selftest_wait_timeout(float(limit_ms)))
 
 
 def sttsm_device_status() -> int:

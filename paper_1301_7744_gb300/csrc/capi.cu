@@ -314,6 +314,17 @@ int sttsm_workspace_size(int m, int64_t n, int64_t p, int b, int prec, size_t* b
 
 int sttsm_device_status(void) { return take_status(); }
 
+int sttsm_selftest_wait_timeout(double limit_ms)
+{
+    if (!(limit_ms > 0.0) || limit_ms > 1000.0) return STTSM_ERR_ARG;
+    int* st = status_dev();
+    if (!st) return STTSM_ERR_CUDA;
+    if (take_status() != 0) return STTSM_ERR_TIMEOUT;   // an earlier timeout is reported first
+    if (launch_wait_probe(st, (unsigned long long)(limit_ms * 1e6), nullptr) != 0) return STTSM_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return STTSM_ERR_CUDA;
+    return take_status() != 0 ? STTSM_ERR_TIMEOUT : STTSM_OK;
+}
+
 int sttsm_set_small_kernel(int kind)
 {
     if (kind != 0 && kind != 1) return STTSM_ERR_ARG;

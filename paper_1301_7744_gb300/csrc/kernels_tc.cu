@@ -724,4 +724,26 @@ int launch_level_tc(int npiece, const TcInst& inst0, const TcInst* d_insts, cons
     return (int)cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ bounded-wait probe
+
+// One thread waits on an mbarrier that no thread ever arrives on, with the
+// same bounded-wait loop the level kernels use but a caller-given limit; on
+// timeout it raises the status word exactly as a level kernel would, and the
+// CTA leaves.  It exercises the failure path without faulting the GPU.
+__global__ void wait_probe_kernel(int* status, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = ptx::smem_u32(&bar);
+    ptx::mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!ptx::mbar_wait_for(b, 0, limit_ns)) atomicExch(status, 1);
+}
+
+int launch_wait_probe(int* d_status, unsigned long long limit_ns, cudaStream_t s)
+{
+    wait_probe_kernel<<<1, 32, 0, s>>>(d_status, limit_ns);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace sttsm

@@ -68,6 +68,9 @@ struct TmaInst {
 // b16: every instance of the launch has b = 16 (two 16-wide blocks per stage);
 // otherwise every instance has b a multiple of 32.
 constexpr int TMA_OUT_PIECES = 0, TMA_OUT_C = 1, TMA_OUT_F32 = 2;
+
+// A wait that never completes, bounded by limit_ns; raises *d_status on timeout.
+int launch_wait_probe(int* d_status, unsigned long long limit_ns, cudaStream_t s);
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
                      int num_sms, int* d_status, int out_kind, bool b16, cudaStream_t s);
 int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s);
