@@ -184,6 +184,20 @@ typedef struct {
  * Tbl. 4 flop count).  Returns the chosen b (> 0) or an sttsm_status. */
 int sttsm_autotune_b(int m, int64_t n, int64_t p, int prec, const int* cands, int ncand);
 
+/* Block size by measurement: for every candidate b the call allocates device
+ * buffers of that shape (A, X, C, workspace), fills A and X with a
+ * deterministic non-zero pattern, runs sttsm_bcss once to warm up and `reps`
+ * times under CUDA events, and keeps the candidate with the smallest median.
+ * Candidates that are invalid or do not fit in 90 % of the free device memory
+ * are skipped (times_ms entry -1).  The choice is cached per (device, m, n,
+ * p, prec, candidate list); with times_ms == NULL a cached choice is returned
+ * without measuring, with times_ms (ncand entries) every candidate is
+ * measured again and its median (ms) written.  Synchronises the device and
+ * allocates (cudaMalloc) for the duration of the call.  Returns the chosen b
+ * or an sttsm_status (STTSM_ERR_UNSUPPORTED if no candidate ran). */
+int sttsm_autotune_b_measured(int m, int64_t n, int64_t p, int prec, const int* cands, int ncand, int reps,
+                              double* times_ms);
+
 /* Batch plan: many independent instances (different m, n, p, b) run as one
  * sequence of launches — per wave, one X-split launch and one launch per
  * level d covering the level-d tiles of every instance with m > d (Fig. 5's

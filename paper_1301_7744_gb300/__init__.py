@@ -91,6 +91,8 @@ def _load():
     L.sttsm_selftest_wait_timeout.restype = i32
     L.sttsm_autotune_b.argtypes = [i32, i64, i64, i32, P, i32]
     L.sttsm_autotune_b.restype = i32
+    L.sttsm_autotune_b_measured.argtypes = [i32, i64, i64, i32, P, i32, i32, P]
+    L.sttsm_autotune_b_measured.restype = i32
     L.sttsm_batch_plan_create.argtypes = [P, i32, i32, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]
     L.sttsm_batch_plan_create.restype = i32
     L.sttsm_batch_workspace_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
@@ -130,12 +132,13 @@ def _load():
 def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points this binding loads."""
     return ["bcss_num_blocks", "bcss_num_elems", "bcss_block_rank", "bcss_block_unrank", "sttsm_flops",
-            "bcss_pack", "bcss_unpack", "sttsm_workspace_size", "sttsm_bcss", "sttsm_bcss_host",
-            "sttsm_device_status", "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read",
-            "sttsm_bcss_noalloc", "sttsm_autotune_b", "sttsm_batch_plan_create", "sttsm_batch_workspace_size",
+            "bcss_pack", "bcss_unpack", "sttsm_workspace_size", "sttsm_bcss", "sttsm_bcss_all_but_one",
+            "sttsm_all_but_one_elems", "sttsm_all_but_one_flops", "sttsm_bcss_host", "sttsm_autotune_b",
+            "sttsm_autotune_b_measured", "sttsm_batch_plan_create", "sttsm_batch_workspace_size",
             "sttsm_batch_info", "sttsm_batch_run", "sttsm_batch_plan_destroy", "sttsm_batch", "sttsm_serve_create",
             "sttsm_serve_submit", "sttsm_serve_poll", "sttsm_serve_stats", "sttsm_serve_destroy",
-            "sttsm_set_small_kernel"]
+            "sttsm_bcss_noalloc", "sttsm_set_small_kernel", "sttsm_device_status", "sttsm_selftest_wait_timeout",
+            "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read"]
 
 
 def _check(fn: str, rc: int) -> None:
@@ -303,6 +306,22 @@ def sttsm_autotune_b(m: int, n: int, p: int, prec: int, cands=(4, 8, 16)) -> int
     if rc <= 0:
         raise SttsmError("sttsm_autotune_b", rc)
     return int(rc)
+
+
+def sttsm_autotune_b_measured(m: int, n: int, p: int, prec: int, cands=(16, 32, 64), reps: int = 3,
+                              with_times: bool = True):
+    """Block size by timing each candidate on the device (see the header); returns
+    (b, {candidate: median ms or None}) with with_times, else (b, None) using the
+    library's cache when it has this shape."""
+    import numpy as np
+    c = np.array(cands, dtype=np.int32)
+    t = np.full(len(cands), -1.0) if with_times else None
+    b = _load().sttsm_autotune_b_measured(m, n, p, prec, c.ctypes.data, len(cands), reps,
+                                          t.ctypes.data if t is not None else None)
+    if b < 0:
+        _check("sttsm_autotune_b_measured", b)
+    times = {int(k): (float(v) if v >= 0 else None) for k, v in zip(cands, t)} if t is not None else None
+    return int(b), times
 
 
 def _descs(instances):

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(st):
     assert "sttsm_bcss" in names and "bcss_pack" in names
     for name in names:
         assert hasattr(lib, name), name
-    assert set(st.exported_symbols()) <= set(names)
+    assert set(st.exported_symbols()) == set(names)
 
 
 @pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6])
@@ -134,3 +134,17 @@ def test_serving_arrivals_are_poisson():
     for _, m, n, p in rq:
         lo, hi = {3: (64, 512), 4: (32, 160), 5: (16, 64), 6: (8, 32)}[m]
         assert lo <= n <= hi and lo <= p <= hi
+
+
+def test_measured_autotune_rejects_bad_arguments_on_the_host(st):
+    import ctypes
+    import numpy as np
+    L = ctypes.CDLL(str(st.lib_path()))
+    f = L.sttsm_autotune_b_measured
+    f.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.c_int, ctypes.c_void_p]
+    c = np.array([16, 32], dtype=np.int32)
+    assert f(3, 100, 100, st.STTSM_BF16X6, None, 2, 3, None) == st.STTSM_ERR_ARG
+    assert f(3, 100, 100, st.STTSM_BF16X6, c.ctypes.data, 0, 3, None) == st.STTSM_ERR_ARG
+    assert f(3, 100, 100, st.STTSM_BF16X6, c.ctypes.data, 2, 0, None) == st.STTSM_ERR_ARG
+    assert f(3, 100, 100, st.STTSM_TF32X3, c.ctypes.data, 2, 3, None) == st.STTSM_ERR_UNSUPPORTED

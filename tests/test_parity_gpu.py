@@ -340,3 +340,15 @@ def test_small_contraction_kernels(st, kind, m, n, p, b):
     finally:
         st.sttsm_set_small_kernel(0)
     assert rel_fro(got, oracle_C_bcss(A, X, m, p, b)) <= 1e-6
+
+
+@pytest.mark.parametrize("precname,cands", [("bf16x6", (16, 32, 64)), ("fp64", (8, 16))])
+def test_measured_autotune(st, precname, cands):
+    """Each candidate is timed; the choice is the fastest median and is cached."""
+    prec = prec_of(st, precname)
+    b, times = st.sttsm_autotune_b_measured(3, 200, 180, prec, cands, reps=2)
+    assert b in cands and all(times[c] is not None and times[c] > 0 for c in cands)
+    assert times[b] == min(times.values())
+    b2, none = st.sttsm_autotune_b_measured(3, 200, 180, prec, cands, reps=2, with_times=False)
+    assert b2 == b and none is None
+    assert st.sttsm_device_status() == 0
