@@ -340,8 +340,16 @@ def fp64_path(st, torch, Xh, b, F, ms):
     ws64 = st.workspace_tensor(M, N, P, b, st.STTSM_FP64)
     tot64, _ = time_steps(torch, lambda: st.sttsm_bcss(A64, dX64, M, N, P, b, C64, st.STTSM_FP64, ws64), 2, 1)
     ms64 = tot64 / 2
-    return ({"value": F / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
-             "speedup_of_split_path": ms64 / ms}, C64)
+    # FP64 reference rate on this GPU: a library FP64 GEMM (4096^3) timed the same way
+    g = 4096
+    ga = torch.randn(g, g, dtype=torch.float64, device="cuda")
+    gb = torch.randn(g, g, dtype=torch.float64, device="cuda")
+    totg, _ = time_steps(torch, lambda: torch.matmul(ga, gb), 3, 1)
+    dgemm = 2.0 * g ** 3 / (totg / 3 * 1e-3) / 1e12
+    del ga, gb
+    value = F / (ms64 * 1e-3) / 1e12
+    return ({"value": value, "unit": "TFLOP/s", "ms_per_step": ms64, "speedup_of_split_path": ms64 / ms,
+             "library_fp64_gemm_tflops": dgemm, "frac_of_library_fp64_gemm": value / dgemm}, C64)
 
 
 def check_and_baseline(args, C, C64, Xh, X32, b, F, world):
