@@ -462,7 +462,7 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
             for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
             const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
             ProfScope ps(stream, 3, d, lflops);
-            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d < nlev - 1 ? TMA_OUT_PIECES : (d == m - 1 ? TMA_OUT_C : TMA_OUT_F32), b == 16, stream));
+            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d < nlev - 1 ? TMA_OUT_PIECES : (d == m - 1 ? TMA_OUT_C : TMA_OUT_F32), b == 16, P->maxcols[d], stream));
             if (rc != STTSM_OK) return rc;
         }
         return STTSM_OK;

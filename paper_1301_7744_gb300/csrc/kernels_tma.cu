@@ -57,6 +57,10 @@ struct SmemT {
     static constexpr int B_PLANE = TC_BN * TC_KC * 2;
     static constexpr int STAGE = NP * (A_PLANE + B_PLANE);
     static constexpr int STAGES = NP == 3 ? 3 : 4;
+    // launches whose tiles are all <= 64 columns: X planes of 64 rows, more stages
+    static constexpr int NSTAGE = NP * (A_PLANE + B_PLANE / 4);
+    static constexpr int NSTAGES = STAGES * STAGE / NSTAGE;
+    static constexpr int MAXST = NSTAGES > STAGES ? NSTAGES : STAGES;
     static constexpr int BYTES = STAGES * STAGE + 1024 + 256;
 };
 
@@ -72,29 +76,44 @@ __device__ __forceinline__ void tmem_fold64(float* acc, uint32_t taddr)
     }
 }
 
+// acc[0..n) += n consecutive TMEM columns (n a multiple of 8, < 64)
+__device__ __forceinline__ void tmem_fold_n(float* acc, uint32_t taddr, int n)
+{
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        if (c * 8 >= n) break;
+        float v[8];
+        tmem_ld_32x32b_x8(taddr + c * 8, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
+    }
+}
+
 }  // namespace
 
 template <int NP, int OUT, bool B16>
 __global__ void __launch_bounds__(T_THREADS, 1)
 level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restrict__ insts,
-                 const Tile* __restrict__ tiles, int ntiles, int* status)
+                 const Tile* __restrict__ tiles, int ntiles, int* status, int narrow)
 {
     using S = SmemT<NP>;
-    constexpr int STAGES = S::STAGES;
+    constexpr int MAXST = S::MAXST;
+    const int STAGES = narrow ? S::NSTAGES : S::STAGES;
+    const int STAGE_BYTES = narrow ? S::NSTAGE : S::STAGE;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = (uint64_t*)(smem + STAGES * S::STAGE);
-    uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 4);
+    uint64_t* bars = (uint64_t*)(smem + S::STAGES * S::STAGE);
+    uint32_t* tmem_holder = (uint32_t*)(bars + 2 * MAXST + 4);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
-    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
-    const uint32_t d0_full = bar0 + 8u * (2 * STAGES);
-    const uint32_t d0_empty = bar0 + 8u * (2 * STAGES + 1);
-    const uint32_t d1_empty = bar0 + 8u * (2 * STAGES + 2);
-    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 3);
+    auto empty_bar = [&](int s) { return bar0 + 8u * (MAXST + s); };
+    const uint32_t d0_full = bar0 + 8u * (2 * MAXST);
+    const uint32_t d0_empty = bar0 + 8u * (2 * MAXST + 1);
+    const uint32_t d1_empty = bar0 + 8u * (2 * MAXST + 2);
+    const uint32_t drain_bar = bar0 + 8u * (2 * MAXST + 3);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
@@ -127,6 +146,12 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             bool ok = true;
             for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
                 const Tile t = tiles[ti];
+                if (narrow && t.ncols > 64) {   // a stage has room for 64 X rows only
+                    *abort_flag = 1;
+                    atomicExch(status, 1);
+                    ok = false;
+                    break;
+                }
                 const TmaInst& TI = insts ? insts[t.inst] : inst0;
                 const LevelInst& I = TI.L;
                 const int pr = t.row0 / I.R, rr0 = t.row0 - pr * I.R;
@@ -136,7 +161,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 for (int ks = 0; ks < nk; ++ks) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                     const int k0 = ks * TC_KC;
-                    const uint32_t sA = smem_u32(smem + stage * S::STAGE);
+                    const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
                     const uint32_t sB = sA + NP * S::A_PLANE;
                     // X box rows: the smallest of 256 / 128 / 64 that covers the tile's columns
                     const int xsel = t.ncols > 128 ? 0 : (t.ncols > 64 ? 1 : 2);
@@ -223,7 +248,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     }
                     if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t sA = smem_u32(smem + stage * S::STAGE);
+                    const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
                     const uint32_t sB = sA + NP * S::A_PLANE;
                     auto adesc = [&](int s, int kh) {
                         if (b16) {
@@ -277,9 +302,8 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
         // ------------------------------------------------------------ epilogue (warps 0-15)
         // warp (quad, cq) owns TMEM lanes 32 quad.. (rows) and the cq-th quarter
         // of the tile's columns (a multiple of 8, <= 64), so narrow tiles keep
-        // all 16 warps busy.  The fold always reads 64 columns from the warp's
-        // base (inside the accumulator's 256 columns for every quarter size);
-        // columns past the quarter are never stored.
+        // all 16 warps busy.  The fold reads the quarter's own columns (all 64
+        // of a full quarter with a fixed-length loop).
         const int quad = warp & 3, cq = warp >> 2;
         const int row = quad * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
@@ -303,13 +327,13 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 if (!mbar_wait(d0_full, group_phase, abort_flag, status)) { ok = false; break; }
                 group_phase ^= 1u;
                 tc_fence_after();
-                if (active) tmem_fold64(acc, tmem_d0 + lane_off + (uint32_t)colbase);
+                if (active) { if (cw == 64) tmem_fold64(acc, tmem_d0 + lane_off + (uint32_t)colbase); else tmem_fold_n(acc, tmem_d0 + lane_off + (uint32_t)colbase, cw); }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(d0_empty);
             }
             if (!ok) break;
-            if (active) tmem_fold64(acc, tmem_d1 + lane_off + (uint32_t)colbase);
+            if (active) { if (cw == 64) tmem_fold64(acc, tmem_d1 + lane_off + (uint32_t)colbase); else tmem_fold_n(acc, tmem_d1 + lane_off + (uint32_t)colbase, cw); }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(d1_empty);
@@ -327,7 +351,8 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
 #pragma unroll
                     for (int e = 0; e < 64; ++e) {
-                        if (e < nvalid) dst[(int64_t)bk * c] = acc[e];
+                        if (e >= nvalid) break;
+                        dst[(int64_t)bk * c] = acc[e];
                         if (++c == b) { c = 0; dst += I.P_out * I.bm; }
                     }
                 } else if constexpr (OUT == TMA_OUT_C) {
@@ -336,7 +361,8 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     // child's block, and b (a multiple of 32) keeps groups of 4 inside blocks
 #pragma unroll
                     for (int e = 0; e < 64; e += 4) {
-                        if (e < nvalid) *(float4*)(dst + c) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                        if (e >= nvalid) break;
+                        *(float4*)(dst + c) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
                         c += 4;
                         if (c == b) { c = 0; dst += I.P_out * I.bm; }
                     }
@@ -351,17 +377,16 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                                          rowoff + (int64_t)bk * c;
 #pragma unroll
                     for (int e = 0; e < 64; e += 2) {
-                        if (e < nvalid) {
-                            float2 x = make_float2(acc[e], acc[e + 1]);
+                        if (e >= nvalid) break;
+                        float2 x = make_float2(acc[e], acc[e + 1]);
 #pragma unroll
-                            for (int pc = 0; pc < NP; ++pc) {
-                                const __nv_bfloat162 h = __float22bfloat162_rn(x);
-                                dst[pc * bm] = h.x;
-                                dst[pc * bm + bk] = h.y;
-                                const float2 f = __bfloat1622float2(h);
-                                x.x -= f.x;
-                                x.y -= f.y;
-                            }
+                        for (int pc = 0; pc < NP; ++pc) {
+                            const __nv_bfloat162 h = __float22bfloat162_rn(x);
+                            dst[pc * bm] = h.x;
+                            dst[pc * bm + bk] = h.y;
+                            const float2 f = __bfloat1622float2(h);
+                            x.x -= f.x;
+                            x.y -= f.y;
                         }
                         c += 2;
                         if (c == b) {
@@ -447,7 +472,7 @@ int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, i
 
 template <int NP, int OUT, bool B>
 static int launch_tma_variant(const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles, int grid,
-                              int* d_status, cudaStream_t s)
+                              int* d_status, int narrow, cudaStream_t s)
 {
     static std::mutex mu;
     static bool attr_set[64] = {};
@@ -462,36 +487,38 @@ static int launch_tma_variant(const TmaInst& inst0, const TmaInst* d_insts, cons
             attr_set[dev] = true;
         }
     }
-    level_tma_kernel<NP, OUT, B><<<grid, T_THREADS, SmemT<NP>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
+    level_tma_kernel<NP, OUT, B><<<grid, T_THREADS, SmemT<NP>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status,
+                                                                            narrow);
     return (int)cudaGetLastError();
 }
 
 template <int NP, int OUT>
 static int launch_tma_b(bool b16, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                        int grid, int* d_status, cudaStream_t s)
+                        int grid, int* d_status, int narrow, cudaStream_t s)
 {
-    return b16 ? launch_tma_variant<NP, OUT, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s)
-               : launch_tma_variant<NP, OUT, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    return b16 ? launch_tma_variant<NP, OUT, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s)
+               : launch_tma_variant<NP, OUT, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
 }
 
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, int out_kind, bool b16, cudaStream_t s)
+                     int num_sms, int* d_status, int out_kind, bool b16, int max_cols, cudaStream_t s)
 {
+    const int narrow = max_cols <= 64 ? 1 : 0;
     if (ntiles <= 0) return 0;
     if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
     if (out_kind < TMA_OUT_PIECES || out_kind > TMA_OUT_F32) return (int)cudaErrorInvalidValue;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
     if (npiece == 2) {
         switch (out_kind) {
-        case TMA_OUT_PIECES: return launch_tma_b<2, TMA_OUT_PIECES>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-        case TMA_OUT_C: return launch_tma_b<2, TMA_OUT_C>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-        default: return launch_tma_b<2, TMA_OUT_F32>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+        case TMA_OUT_PIECES: return launch_tma_b<2, TMA_OUT_PIECES>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+        case TMA_OUT_C: return launch_tma_b<2, TMA_OUT_C>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+        default: return launch_tma_b<2, TMA_OUT_F32>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
         }
     }
     switch (out_kind) {
-    case TMA_OUT_PIECES: return launch_tma_b<3, TMA_OUT_PIECES>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    case TMA_OUT_C: return launch_tma_b<3, TMA_OUT_C>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
-    default: return launch_tma_b<3, TMA_OUT_F32>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    case TMA_OUT_PIECES: return launch_tma_b<3, TMA_OUT_PIECES>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+    case TMA_OUT_C: return launch_tma_b<3, TMA_OUT_C>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+    default: return launch_tma_b<3, TMA_OUT_F32>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
     }
 }
 

@@ -71,8 +71,10 @@ constexpr int TMA_OUT_PIECES = 0, TMA_OUT_C = 1, TMA_OUT_F32 = 2;
 
 // A wait that never completes, bounded by limit_ns; raises *d_status on timeout.
 int launch_wait_probe(int* d_status, unsigned long long limit_ns, cudaStream_t s);
+// max_cols: the widest tile of the launch; launches of tiles <= 64 columns wide
+// run with more, smaller pipeline stages.
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, int out_kind, bool b16, cudaStream_t s);
+                     int num_sms, int* d_status, int out_kind, bool b16, int max_cols, cudaStream_t s);
 int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s);
 
 // Tensor maps of a BF16-piece parent array with nblocks stored blocks (all

@@ -1,4 +1,5 @@
 // plan.cu — host-side level plans (see plan.h).
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -129,7 +130,7 @@ const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN)
     auto it = g_plans.find(key);
     if (it != g_plans.end()) return it->second;
     DevPlan* P = new DevPlan();
-    for (int d = 0; d < STTSM_MAX_M; ++d) { P->d_tiles[d] = nullptr; P->d_G[d] = nullptr; P->ntiles[d] = 0; }
+    for (int d = 0; d < STTSM_MAX_M; ++d) { P->d_tiles[d] = nullptr; P->d_G[d] = nullptr; P->ntiles[d] = 0; P->maxcols[d] = 0; }
     if (make_shape(m, n, p, b, &P->shape) != STTSM_OK) { delete P; return nullptr; }
     P->BM = BM;
     P->BN = BN;
@@ -139,6 +140,7 @@ const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN)
         build_level_tiles(P->shape, d, BM, BN, 0, tiles);
         build_level_G(P->shape, d, G);
         P->ntiles[d] = (int)tiles.size();
+        for (const Tile& t : tiles) P->maxcols[d] = std::max(P->maxcols[d], (int)t.ncols);
         if (cudaMalloc(&P->d_tiles[d], tiles.size() * sizeof(Tile)) != cudaSuccess ||
             cudaMalloc(&P->d_G[d], G.size() * sizeof(int32_t)) != cudaSuccess ||
             cudaMemcpy(P->d_tiles[d], tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess ||

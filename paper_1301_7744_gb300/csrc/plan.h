@@ -52,6 +52,7 @@ struct DevPlan {
     Shape shape;
     int BM, BN;
     int ntiles[STTSM_MAX_M];
+    int maxcols[STTSM_MAX_M];   // widest tile of each level
     Tile* d_tiles[STTSM_MAX_M];
     int32_t* d_G[STTSM_MAX_M];
 };

@@ -305,8 +305,12 @@ int launch_step(sttsm_serve_s* H)
         if (k == 0) lrc = launch_level_tc(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, H->stream);
         else if (k == 1 && small_kernel_kind() == 0) lrc = launch_level_small_f32_tc((const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->stream);
         else if (k == 1) lrc = launch_level_tc_small(H->np, dummy, (const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->status, H->stream);
-        else lrc = launch_level_tma(H->np, tdummy, (const TmaInst*)(S.d + o_ti[k - 2]), dt, n, H->sms, H->status,
-                                    (k & 1) == 1 ? TMA_OUT_C : TMA_OUT_PIECES, k >= 4, H->stream);
+        else {
+            int maxc = 0;
+            for (const Tile& t : tiles[k]) maxc = std::max(maxc, (int)t.ncols);
+            lrc = launch_level_tma(H->np, tdummy, (const TmaInst*)(S.d + o_ti[k - 2]), dt, n, H->sms, H->status,
+                                   (k & 1) == 1 ? TMA_OUT_C : TMA_OUT_PIECES, k >= 4, maxc, H->stream);
+        }
         if (lrc != 0) return STTSM_ERR_CUDA;
     }
     H->cur ^= 1;
