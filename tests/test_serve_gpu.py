@@ -25,9 +25,10 @@ def st():
     return pkg
 
 
-def make_request(st, i, m, n, p):
+def make_request(st, i, m, n, p, b=None):
     cands = {3: (16, 32), 4: (8, 16), 5: (4, 8), 6: (4, 8)}[m]
-    b = st.sttsm_autotune_b(m, n, p, st.STTSM_BF16X6, cands)
+    if b is None:
+        b = st.sttsm_autotune_b(m, n, p, st.STTSM_BF16X6, cands)
     A = synth.sym_uniform_dense(m, n, 300 + i)
     X = synth.x_gaussian(400 + i, p, n).astype(np.float32).astype(np.float64)
     Ab = device_bcss_from_dense(st, A, m, n, b, torch.float32)
@@ -123,3 +124,20 @@ def test_busy_queue_and_over_budget_request(st):
     wait_all(srv, [t_big])
     srv.destroy()
     assert st.STTSM_ERR_BUSY in codes and 0 in codes
+
+
+def test_both_tma_forms_and_small_tiles_in_one_step(st):
+    """Requests that run on the TMA-fed kernel with b = 16 and with b = 32, and on the
+    short-contraction kernel, admitted together: every step launches each form over its
+    own requests; each result equals the request run alone and the oracle's."""
+    shapes = [(3, 100, 90, 16), (3, 96, 96, 32), (4, 70, 40, 16), (3, 130, 70, 32), (5, 16, 16, 4), (3, 24, 24, 8)]
+    reqs = [make_request(st, 7000 + i, m, n, p, b) for i, (m, n, p, b) in enumerate(shapes)]
+    torch.cuda.synchronize()
+    srv = st.Server(4 << 30)
+    tickets = [srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"]) for r in reqs]
+    wait_all(srv, tickets)
+    srv.destroy()
+    for r in reqs:
+        got = r["C"].double().cpu().numpy()
+        assert np.array_equal(got, alone(st, r)), (r["m"], r["n"], r["b"])
+        assert rel_fro(got, oracle_C_bcss(r["A"], r["X"], r["m"], r["p"], r["b"])) <= 1e-6
