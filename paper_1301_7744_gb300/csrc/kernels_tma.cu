@@ -358,7 +358,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 } else if constexpr (OUT == TMA_OUT_C) {
                     float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
                     // the FP32 output is C (k = 0): a row's columns are contiguous within a
-                    // child's block, and b (a multiple of 32) keeps groups of 4 inside blocks
+                    // child's block, and b (16 or a multiple of 32) keeps groups of 4 inside blocks
 #pragma unroll
                     for (int e = 0; e < 64; e += 4) {
                         if (e >= nvalid) break;
