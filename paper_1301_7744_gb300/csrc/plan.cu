@@ -91,15 +91,20 @@ void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std:
             for (int t = 0; t < d; ++t) child_base += binom_small((int64_t)u[t] + t + 1, t + 2);
         }
         const int64_t ncols = children * s.b;
+        // wide tiles (BN >= 128): a parent's columns are cut into equal widths (a
+        // multiple of 16) rather than full tiles plus a narrow remainder
+        int64_t w = BN;
+        const int64_t nct = (ncols + BN - 1) / BN;
+        if (BN >= 128 && nct > 1) w = ((ncols + nct - 1) / nct + 15) / 16 * 16;
         for (int64_t r0 = 0; r0 < rows; r0 += BM) {
-            for (int64_t c0 = 0; c0 < ncols; c0 += BN) {
+            for (int64_t c0 = 0; c0 < ncols; c0 += w) {
                 Tile t;
                 t.inst = inst;
                 t.parent = (int32_t)par;
                 t.child_base = (int32_t)child_base;
                 t.row0 = (int32_t)r0;
                 t.col0 = (int32_t)c0;
-                t.ncols = (int32_t)(ncols - c0 < BN ? ncols - c0 : BN);
+                t.ncols = (int32_t)(ncols - c0 < w ? ncols - c0 : w);
                 t.pad0 = t.pad1 = 0;
                 tiles.push_back(t);
             }

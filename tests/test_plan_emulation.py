@@ -93,9 +93,15 @@ def test_plan_emulation_matches_oracle(st, m, n, p, b, precname):
 
 
 def test_tile_columns_stay_within_x_rows(st):
-    """Columns of every tile index rows of the padded X (pbar * b rows)."""
+    """Columns of every tile index rows of the padded X (pbar * b rows); a parent's
+    columns are cut into equal widths (multiples of 16, <= 256) that cover them once."""
     m, n, p, b = 3, 768, 768, 64
     for d in range(m):
         tiles, _, info = st.sttsm_plan_level(m, n, p, b, st.STTSM_BF16X6, d)
         assert np.all(tiles[:, 4] + tiles[:, 5] <= 12 * 64)
-        assert np.all(tiles[:, 5] <= 256) and np.all(tiles[:, 5] % 64 == 0)
+        assert np.all(tiles[:, 5] <= 256) and np.all(tiles[:, 5] % 16 == 0) and np.all(tiles[:, 4] % 16 == 0)
+        # per (parent, row0): widths differ by at most 16 apart from the last one
+        key = tiles[:, 1].astype(np.int64) * (1 << 32) + tiles[:, 3]
+        for k in np.unique(key)[:200]:
+            w = tiles[key == k, 5]
+            assert w.sum() == ((tiles[key == k, 4] + w).max()) and (len(w) == 1 or w[:-1].min() >= w.max() - 16)
