@@ -308,41 +308,51 @@ __device__ __forceinline__ void s32_issue(S32Stage& S, const Desc* insts, const 
     }
 }
 
+// Two FP32 fused multiply-adds in one instruction: lanes (lo, hi) of d get
+// d + a * x lane by lane, each rounded once like fmaf.  Pairs hold two
+// consecutive output columns; a2 holds one operand entry twice.
+__device__ __forceinline__ void s32_fma2(uint64_t& d, uint64_t a2, uint64_t x2)
+{
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a2), "l"(x2));
+}
+__device__ __forceinline__ uint64_t s32_dup(float a)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+
 // Rows times the tile's X block, then the scatter into the children's blocks:
 // output (child cb + jb, block pr) at in-block offset OFF[k][rr] + b^k c.
 // A thread computes TR rows (t mod 128/TR, + 128/TR, ...) times NC/TR columns
 // (part t / (128/TR)), so every X value read from shared memory feeds TR
-// products.
+// products; column pairs go through the two-lane FMA.
 template <int NC, int TR>
 __device__ __forceinline__ void s32_compute_store(const S32Stage& S, const LevelInst& I, const Tile& t)
 {
     constexpr int TC = NC / TR, RSTEP = S32_ROWS / TR;
     const int r0 = threadIdx.x % RSTEP, part = threadIdx.x / RSTEP;
     const int Kc = (I.Ktot + 3) & ~3;
-    float acc[TR][TC];
+    uint64_t acc[TR][TC / 2];
 #pragma unroll
     for (int j = 0; j < TR; ++j)
 #pragma unroll
-        for (int c = 0; c < TC; ++c) acc[j][c] = 0.f;
-#pragma unroll 2
+        for (int c = 0; c < TC / 2; ++c) acc[j][c] = 0ull;
+#pragma unroll 1
     for (int kk = 0; kk < Kc; kk += 4) {
-        float av[4][TR];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int j = 0; j < TR; ++j) av[u][j] = S.A[kk + u][r0 + j * RSTEP];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float4* xr = (const float4*)&S.X[kk + u][part * TC];
+            const ulonglong2* xr = (const ulonglong2*)&S.X[kk + u][part * TC];
+            uint64_t a2[TR];
+#pragma unroll
+            for (int j = 0; j < TR; ++j) a2[j] = s32_dup(S.A[kk + u][r0 + j * RSTEP]);
 #pragma unroll
             for (int c4 = 0; c4 < TC / 4; ++c4) {
-                const float4 x = xr[c4];
+                const ulonglong2 x = xr[c4];
 #pragma unroll
                 for (int j = 0; j < TR; ++j) {
-                    acc[j][4 * c4 + 0] = fmaf(av[u][j], x.x, acc[j][4 * c4 + 0]);
-                    acc[j][4 * c4 + 1] = fmaf(av[u][j], x.y, acc[j][4 * c4 + 1]);
-                    acc[j][4 * c4 + 2] = fmaf(av[u][j], x.z, acc[j][4 * c4 + 2]);
-                    acc[j][4 * c4 + 3] = fmaf(av[u][j], x.w, acc[j][4 * c4 + 3]);
+                    s32_fma2(acc[j][2 * c4 + 0], a2[j], x.x);
+                    s32_fma2(acc[j][2 * c4 + 1], a2[j], x.y);
                 }
             }
         }
@@ -354,13 +364,17 @@ __device__ __forceinline__ void s32_compute_store(const S32Stage& S, const Level
     for (int j = 0; j < TR; ++j) {
         const int g = t.row0 + r0 + j * RSTEP;
         if (g >= I.rows_per_parent) continue;
+        float res[TC];
+#pragma unroll
+        for (int e = 0; e < TC / 2; ++e)
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(res[2 * e]), "=f"(res[2 * e + 1]) : "l"(acc[j][e]));
         const int pr = g / I.R, rr = g - pr * I.R;
         const int64_t rowoff = __ldg(I.OFF + I.k * I.R + rr);
         int jb = cfirst / b, c = cfirst - jb * b;
         float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
 #pragma unroll
         for (int e = 0; e < TC; ++e) {
-            if (e < nvalid) dst[(int64_t)bk * c] = acc[j][e];
+            if (e < nvalid) dst[(int64_t)bk * c] = res[e];
             if (++c == b) { c = 0; dst += I.P_out * I.bm; }
         }
     }

@@ -375,6 +375,12 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     const int64_t child_step = (int64_t)I.P_out * NP * bm;
                     __nv_bfloat16* dst = (__nv_bfloat16*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * NP * bm +
                                          rowoff + (int64_t)bk * c;
+                    // lanes 2i and 2i+1 hold adjacent rows (contiguous: k >= 1 and b^k >= 16):
+                    // after one exchange the even lane stores column e of both rows, the odd
+                    // lane column e+1, each as one 4-byte store
+                    const bool odd = lane & 1;
+                    const uint32_t sel = odd ? 0x3276u : 0x5410u;
+                    const int64_t soff = odd ? (int64_t)bk - 1 : 0;
 #pragma unroll
                     for (int e = 0; e < 64; e += 2) {
                         if (e >= nvalid) break;
@@ -382,8 +388,9 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
 #pragma unroll
                         for (int pc = 0; pc < NP; ++pc) {
                             const __nv_bfloat162 h = __float22bfloat162_rn(x);
-                            dst[pc * bm] = h.x;
-                            dst[pc * bm + bk] = h.y;
+                            const uint32_t hv = *(const uint32_t*)&h;
+                            const uint32_t pv = __shfl_xor_sync(0xffffffffu, hv, 1);
+                            *(uint32_t*)(dst + pc * bm + soff) = __byte_perm(hv, pv, sel);
                             const float2 f = __bfloat1622float2(h);
                             x.x -= f.x;
                             x.y -= f.y;

@@ -123,7 +123,9 @@ def test_config1_rank2_closed_form(st, precname):
 SHAPES = [(1, 10, 7, 4), (2, 9, 11, 3), (2, 130, 70, 32), (3, 17, 5, 6), (3, 40, 40, 4), (3, 100, 100, 32),
           (3, 96, 96, 48), (4, 13, 9, 4), (4, 20, 12, 5), (5, 7, 6, 2), (5, 16, 16, 8), (6, 6, 5, 2), (3, 130, 130, 64),
           (3, 100, 90, 16), (3, 70, 130, 16), (3, 144, 40, 16), (4, 70, 40, 16),
-          (3, 5, 3, 8), (2, 3, 10, 4), (8, 3, 2, 1), (7, 4, 3, 2), (6, 5, 4, 1)]
+          (3, 5, 3, 8), (2, 3, 10, 4), (8, 3, 2, 1), (7, 4, 3, 2), (6, 5, 4, 1),
+          # degenerate: one entry, n = 1 < b, p = 1, m = 1 with n = p = 1
+          (3, 1, 1, 1), (3, 1, 6, 4), (4, 5, 1, 2), (2, 1, 1, 8), (1, 1, 1, 1)]
 
 
 @pytest.mark.parametrize("m,n,p,b", SHAPES)

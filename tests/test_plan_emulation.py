@@ -77,7 +77,9 @@ def emulate(st, m, n, p, b, prec, A_bcss, X, nlev=None):
 
 CASES = [(3, 24, 24, 8), (1, 10, 7, 4), (2, 9, 11, 3), (3, 17, 5, 6), (4, 13, 9, 4), (5, 7, 6, 2), (4, 20, 12, 5),
          (3, 40, 40, 4), (2, 300, 260, 64), (6, 6, 5, 2), (3, 40, 33, 1), (2, 64, 64, 1), (4, 21, 21, 7),
-         (3, 5, 3, 8), (2, 3, 10, 4), (8, 3, 2, 1), (7, 4, 3, 2), (6, 5, 4, 1)]
+         (3, 5, 3, 8), (2, 3, 10, 4), (8, 3, 2, 1), (7, 4, 3, 2), (6, 5, 4, 1),
+         # degenerate: one entry, n = 1 < b, p = 1, m = 1 with n = p = 1
+         (3, 1, 1, 1), (3, 1, 6, 4), (4, 5, 1, 2), (2, 1, 1, 8), (1, 1, 1, 1)]
 
 
 @pytest.mark.parametrize("m,n,p,b", CASES)
