@@ -435,8 +435,8 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
                 rc = cuda_err(launch_split_bcss((const float*)A, ws + w.apieces, s.lv[0].P_parent, s.bm, np, stream));
         }
         if (rc != STTSM_OK) return rc;
-        for (int xs = 0; xs < 3 && rc == STTSM_OK; ++xs)
-            rc = make_x_tensor_map(&tm.tmX[xs], ws + w.xpieces, np, w.rows, w.Kp, TC_BN >> xs);
+        for (int xs = 0; xs < TMA_NX && rc == STTSM_OK; ++xs)
+            rc = make_x_tensor_map(&tm.tmX[xs], ws + w.xpieces, np, w.rows, w.Kp, 32 * (xs + 1));
         if (rc != STTSM_OK) return rc;
         for (int d = 0; d < nlev; ++d) {
             const LevelShape& LS = s.lv[d];

@@ -163,15 +163,15 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     const int k0 = ks * TC_KC;
                     const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
                     const uint32_t sB = sA + NP * S::A_PLANE;
-                    // X box rows: the smallest of 256 / 128 / 64 that covers the tile's columns
-                    const int xsel = t.ncols > 128 ? 0 : (t.ncols > 64 ? 1 : 2);
+                    // X box rows: the tile's columns rounded up to 32
+                    const int xsel = (t.ncols + 31) / 32 - 1;
+                    const uint32_t x_bytes = (uint32_t)(NP * (xsel + 1) * 32 * TC_KC * 2);
                     if (b16) {
                         // two stored blocks per stage, one per 16-wide K slice (the
                         // second is absent in the last stage when n-bar is odd)
                         const int ib0 = k0 >> 4;
                         const int nblk = ib0 + 1 < I.nbar ? 2 : 1;
-                        mbar_arrive_expect_tx(full_bar(stage),
-                                              (uint32_t)(nblk * NP * (S::A_PLANE / 2) + (NP * S::B_PLANE >> xsel)));
+                        mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(nblk * NP * (S::A_PLANE / 2)) + x_bytes);
                         for (int h = 0; h < nblk; ++h) {
                             const int32_t gq = __ldg(Grow + ib0 + h);
                             const int q = gq & 7;
@@ -189,7 +189,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                         const int32_t gq = __ldg(Grow + ib);
                         const int q = gq & 7;
                         const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
-                        mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(NP * S::A_PLANE + (NP * S::B_PLANE >> xsel)));
+                        mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(NP * S::A_PLANE) + x_bytes);
                         if (q == 0) {
                             tma_load_3d(sA, &TI.tmA[0], a0, rr0, bp, full_bar(stage));
                         } else {
@@ -227,8 +227,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int nmma = (t.ncols + 15) & ~15;
                 const uint32_t idesc_k = idesc_bf16(nmma), idesc_mn = idesc_bf16_amn(nmma);
                 // B piece planes are as tall as the X box the producer used
-                const int xsel = t.ncols > 128 ? 0 : (t.ncols > 64 ? 1 : 2);
-                const uint32_t b_plane = (uint32_t)(S::B_PLANE >> xsel);
+                const uint32_t b_plane = (uint32_t)(((t.ncols + 31) / 32) * 32 * TC_KC * 2);
                 if (!mbar_wait(d1_empty, tile_phase ^ 1u, abort_flag, status)) { ok = false; break; }
                 tile_phase ^= 1u;
                 tc_fence_after();

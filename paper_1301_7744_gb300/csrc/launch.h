@@ -57,8 +57,9 @@ int launch_level_tc_small(int npiece, const TcInst& inst0, const TcInst* d_insts
 
 // TMA-fed variant (kernels_tma.cu): parent temporaries (and A) as BF16 pieces
 // [node][block][piece][b^m]; tmA[q] maps the parent for insertion position q.
+constexpr int TMA_NX = 8;
 struct TmaInst {
-    CUtensorMap tmX[3];            // X pieces with box rows 256, 128, 64 (chosen per tile by its columns)
+    CUtensorMap tmX[TMA_NX];       // X pieces with box rows 32 (i + 1); a tile of c columns loads 32 ceil(c / 32) rows
     CUtensorMap tmA[STTSM_MAX_M];
     LevelInst L;
 };

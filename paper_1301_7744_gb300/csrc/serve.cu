@@ -166,11 +166,11 @@ int admit(sttsm_serve_s* H, Req& R)
 {
     const Shape& s = R.s;
     char* base = H->arena_base + R.ws_off;
-    CUtensorMap map, xmaps[3];
+    CUtensorMap map, xmaps[TMA_NX];
     const int box = R.small ? TC_SMALL_BN : TC_BN;
     if (R.tma) {
-        for (int xs = 0; xs < 3; ++xs)
-            if (make_x_tensor_map(&xmaps[xs], base + R.x_off, H->np, R.rows, R.Kp, TC_BN >> xs) != STTSM_OK)
+        for (int xs = 0; xs < TMA_NX; ++xs)
+            if (make_x_tensor_map(&xmaps[xs], base + R.x_off, H->np, R.rows, R.Kp, 32 * (xs + 1)) != STTSM_OK)
                 return STTSM_ERR_CUDA;
     } else if (make_x_tensor_map(&map, base + R.x_off, H->np, R.rows, R.Kp, box) != STTSM_OK) {
         return STTSM_ERR_CUDA;
@@ -206,7 +206,7 @@ int admit(sttsm_serve_s* H, Req& R)
         if (R.tma) {
             TmaInst& M = R.tinst[d];
             memset(&M, 0, sizeof(M));
-            for (int xs = 0; xs < 3; ++xs) M.tmX[xs] = xmaps[xs];
+            for (int xs = 0; xs < TMA_NX; ++xs) M.tmX[xs] = xmaps[xs];
             if (make_a_tensor_maps(M.tmA, L.parent, LS.nodes_parent * LS.P_parent, H->np, s.b, s.m, LS.k) != STTSM_OK)
                 return STTSM_ERR_CUDA;
             M.L = L;
