@@ -360,6 +360,39 @@ __device__ __forceinline__ void s32_compute_store(const S32Stage& S, const Level
     const int b = I.b, bk = I.bpow[I.k];
     const int cfirst = t.col0 + part * TC;
     const int nvalid = t.ncols - part * TC;
+    if (b >= 4 && (b & (b - 1)) == 0) {
+        // b a power of two >= 4: a thread's columns start on a multiple of 4 and
+        // the tile's width is a multiple of b, so every group of 4 columns lies
+        // inside one child block; at k = 0 it is 4 contiguous, 16-byte aligned
+        // floats of the row
+        const int lb = __ffs(b) - 1;
+        const int64_t child_step = (int64_t)I.P_out * I.bm;
+#pragma unroll
+        for (int j = 0; j < TR; ++j) {
+            const int g = t.row0 + r0 + j * RSTEP;
+            if (g >= I.rows_per_parent) continue;
+            const int pr = g / I.R, rr = g - pr * I.R;
+            float* row = (float*)I.out + ((int64_t)t.child_base * I.P_out + pr) * I.bm + __ldg(I.OFF + I.k * I.R + rr);
+#pragma unroll
+            for (int e = 0; e < TC; e += 4) {
+                if (e >= nvalid) break;
+                float r4[4];
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(r4[0]), "=f"(r4[1]) : "l"(acc[j][e / 2]));
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(r4[2]), "=f"(r4[3]) : "l"(acc[j][e / 2 + 1]));
+                const int cc = cfirst + e;
+                float* d = row + (int64_t)(cc >> lb) * child_step + (int64_t)bk * (cc & (b - 1));
+                if (bk == 1) {
+                    *(float4*)d = make_float4(r4[0], r4[1], r4[2], r4[3]);
+                } else {
+                    d[0] = r4[0];
+                    d[bk] = r4[1];
+                    d[2 * bk] = r4[2];
+                    d[3 * bk] = r4[3];
+                }
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < TR; ++j) {
         const int g = t.row0 + r0 + j * RSTEP;
