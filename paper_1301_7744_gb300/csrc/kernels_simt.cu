@@ -264,8 +264,18 @@ __device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, con
         int32_t off[S32_K / 4];
 #pragma unroll
         for (int i = 0; i < S32_K / 4; ++i) gq[i] = ib0 + i < nbar ? __ldg(Grow + ib0 + i) : 0;
+        if (B > 0) {
+            // off_q(rr) = rr mod b^q + b^(q+1) (rr div b^q), b = 2^LB
+            constexpr int LB = B == 4 ? 2 : (B == 8 ? 3 : 4);
 #pragma unroll
-        for (int i = 0; i < S32_K / 4; ++i) off[i] = ib0 + i < nbar ? __ldg(OFF + (gq[i] & 7) * R + rr) : 0;
+            for (int i = 0; i < S32_K / 4; ++i) {
+                const int lq = (gq[i] & 7) * LB;
+                off[i] = (rr & ((1 << lq) - 1)) + ((rr >> lq) << (lq + LB));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < S32_K / 4; ++i) off[i] = ib0 + i < nbar ? __ldg(OFF + (gq[i] & 7) * R + rr) : 0;
+        }
 #pragma unroll
         for (int i = 0; i < S32_K / 4; ++i) {
             if (ib0 + i >= nbar) break;
