@@ -194,9 +194,19 @@ __device__ __forceinline__ int s32_width_class(int ncols)
     return ncols <= 8 ? 0 : ncols <= 16 ? 1 : ncols <= 24 ? 2 : ncols <= 32 ? 3 : ncols <= 48 ? 4 : 5;
 }
 
+// Column offset of contraction row kk of a tile's X block: a warp copies
+// 32 / NCX rows at once (NCX = NC rounded up to a power of two), and rows
+// 64 words apart share banks, so rows of tiles <= 8 (<= 16) columns wide are
+// shifted by 8 (kk mod 4) (16 (kk mod 2)) words.  The compute loop steps kk
+// by 4, so the shift of row kk + u is known at compile time.
+template <int NC>
+__host__ __device__ constexpr int s32_xshift(int kk)
+{
+    return NC <= 8 ? 8 * (kk & 3) : (NC <= 16 ? 16 * (kk & 1) : 0);
+}
+
 // X block of a tile (zero-filled outside the tile and outside X).  Lane
-// t copies column t mod NCX (NCX = NC rounded up to a power of two) of rows
-// t / NCX, t / NCX + 128 / NCX, ...
+// t copies column t mod NCX of rows t / NCX, t / NCX + 128 / NCX, ...
 template <int NC>
 __device__ __forceinline__ void s32_issue_x(S32Stage& S, const LevelInst& I, const Tile& t, int Kc)
 {
@@ -210,7 +220,8 @@ __device__ __forceinline__ void s32_issue_x(S32Stage& S, const LevelInst& I, con
     const int64_t pstep = (int64_t)KSTEP * I.p;
     int kk = threadIdx.x / NCX;
     const float* src = X + j + (int64_t)kk * I.p;
-    uint32_t dst = s32_smem(&S.X[kk][c]);
+    // the shift is the same for all rows of this thread (KSTEP is a multiple of 4)
+    uint32_t dst = s32_smem(&S.X[kk][c + s32_xshift<NC>(kk)]);
     for (; kk < nrows; kk += KSTEP, src += pstep, dst += KSTEP * S32_COLS * 4) s32_cp4(dst, src, 4);
     for (; kk < Kc; kk += KSTEP, dst += KSTEP * S32_COLS * 4) s32_cp4(dst, X, 0);
 }
@@ -352,7 +363,7 @@ __device__ __forceinline__ void s32_compute_store(const S32Stage& S, const Level
     for (int kk = 0; kk < Kc; kk += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const ulonglong2* xr = (const ulonglong2*)&S.X[kk + u][part * TC];
+            const ulonglong2* xr = (const ulonglong2*)&S.X[kk + u][part * TC + s32_xshift<NC>(u)];
             uint64_t a2[TR];
 #pragma unroll
             for (int j = 0; j < TR; ++j) a2[j] = s32_dup(S.A[kk + u][r0 + j * RSTEP]);
