@@ -358,12 +358,28 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
                     // the FP32 output is C (k = 0): a row's columns are contiguous within a
                     // child's block, and b (16 or a multiple of 32) keeps groups of 4 inside blocks
+                    if (((uintptr_t)I.out & 31) == 0) {
+                        // 32-byte stores (a whole sector per lane): c and the row start are
+                        // multiples of 8 floats, and b (a multiple of 16) keeps groups of 8
+                        // inside blocks
 #pragma unroll
-                    for (int e = 0; e < 64; e += 4) {
-                        if (e >= nvalid) break;
-                        *(float4*)(dst + c) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
-                        c += 4;
-                        if (c == b) { c = 0; dst += I.P_out * I.bm; }
+                        for (int e = 0; e < 64; e += 8) {
+                            if (e >= nvalid) break;
+                            asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                                         :: "l"(dst + c), "f"(acc[e]), "f"(acc[e + 1]), "f"(acc[e + 2]), "f"(acc[e + 3]),
+                                            "f"(acc[e + 4]), "f"(acc[e + 5]), "f"(acc[e + 6]), "f"(acc[e + 7])
+                                         : "memory");
+                            c += 8;
+                            if (c == b) { c = 0; dst += I.P_out * I.bm; }
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 64; e += 4) {
+                            if (e >= nvalid) break;
+                            *(float4*)(dst + c) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                            c += 4;
+                            if (c == b) { c = 0; dst += I.P_out * I.bm; }
+                        }
                     }
                 } else {
                     // BF16 pieces of the next level's operand: [node][block][piece][b^m].
