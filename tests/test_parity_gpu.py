@@ -154,6 +154,27 @@ def test_tma_path_taken(st, m, n, p, b):
     assert rel_fro(got, oracle_C_bcss(A, X, m, p, b)) <= TOL["bf16x6"]
 
 
+@pytest.mark.parametrize("m,n,p,b", [(3, 100, 90, 16), (3, 96, 96, 32)])
+def test_c_only_16_byte_aligned(st, m, n, p, b):
+    """The TMA kernel writes C with 32-byte stores when C is 32-byte aligned and
+    with 16-byte stores otherwise: a C that is only 16-byte aligned gets the same
+    bits as an aligned one."""
+    A, X = inputs(m, n, p, seed_a=7, seed_x=8, fp32=True)
+    Ab = device_bcss_from_dense(st, A, m, n, b, torch.float32)
+    aligned = run_sttsm(st, Ab, X, m, n, p, b, st.STTSM_BF16X6)
+    nC = st.bcss_num_elems(m, p, b)
+    big = torch.full((nC + 8,), float("nan"), dtype=torch.float32, device="cuda")
+    C = big[4: 4 + nC]                      # 16 bytes past a 256-byte aligned allocation
+    assert C.data_ptr() % 32 == 16
+    dX = torch.from_numpy(xcol(X)).to(device="cuda", dtype=torch.float32)
+    ws = st.workspace_tensor(m, n, p, b, st.STTSM_BF16X6)
+    st.sttsm_bcss(Ab, dX, m, n, p, b, C, st.STTSM_BF16X6, ws)
+    torch.cuda.synchronize()
+    got = C.double().cpu().numpy()
+    assert np.array_equal(got, aligned)
+    assert rel_fro(got, oracle_C_bcss(A, X, m, p, b)) <= TOL["bf16x6"]
+
+
 def test_bf16x3_two_piece_error_is_reported(st):
     """The 2-piece split (3 products) keeps ~16 bits per operand: its error
     sits near 1e-5, above the 1e-6 target that BF16X6 meets."""
