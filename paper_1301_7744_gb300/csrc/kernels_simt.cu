@@ -154,15 +154,20 @@ int launch_split_x_batch(const SplitDesc* d_desc, int count, int blocks, int npi
 // Level kernel for short contractions (n̄ b <= 64) in FP32 on the CUDA cores,
 // one thread per output row of a 128 x <=64 tile.  A CTA stages one tile at
 // a time in shared memory with cp.async (the tile's A rows, gathered from the
-// stored parent blocks through G / OFF, and its X block); four CTAs share an SM, so the copies of one
-// overlap the arithmetic of the others.  A CTA copies an X block only when
-// it differs from the one of its previous tile.
+// stored parent blocks through G and the in-block offsets off_q, computed
+// with shifts for b in {4, 8, 16} and read from the OFF table otherwise, and
+// its X block); four CTAs share an SM, so the copies of one overlap the
+// arithmetic of the others.  A CTA copies an X block only when it differs
+// from the one of its previous tile.
 // Both operands are kept [kk][...] in shared memory: A[kk][row] (the 4-byte
 // copies of 32 rows and the reads of a contraction row are conflict-free),
 // X[kk][column] read by broadcast.  The column count of a tile selects a
 // compile-time width (8, 16, 24, 32, 48 or 64), so the inner loop has no
 // predicates, and a register blocking (1, 2 or 4 rows per thread) that
-// lets one X read feed several rows.  Every entry is a sequential FP32 sum of <= 64 products.
+// lets one X read feed several rows; column pairs accumulate through the
+// two-lane FMA.  Results of b a power of two >= 4 are stored four columns at a
+// time (one 16-byte store at k = 0).  Every entry is a sequential FP32 sum of
+// <= 64 products.
 // Used where tensor-core tiles of <= 64 columns and <= 64 contraction indices
 // are latency-bound (batches and serving of small instances).
 constexpr int S32_ROWS = 128, S32_COLS = 64, S32_K = 64;
