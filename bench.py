@@ -157,6 +157,42 @@ def make_device_inputs(st, torch, b, dtype):
     return A
 
 
+def pack_bandwidth(st, torch, b, pk, pk_src, reps=5):
+    """bcss_pack (dense -> BCSS) and bcss_unpack (BCSS -> dense) of the FP32
+    workload tensor, CUDA events on the current stream, mean of reps launches
+    after one untimed launch.  Algorithmic bytes: pack reads and writes each
+    stored entry once (4 B each way); unpack writes each dense entry and reads
+    its canonical stored entry (4 B each way)."""
+    import synth
+    stream = torch.cuda.current_stream()
+    dense = torch.empty(N ** M, dtype=torch.float32, device="cuda")
+    synth.dev_sym_uniform_dense(dense.data_ptr(), M, N, SEED_A, "f32", stream.cuda_stream)
+    A = torch.empty(st.bcss_num_elems(M, N, b), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(dense)
+    res = {}
+    for name, fn, nbytes in (("pack", lambda: st.bcss_pack(dense, A, M, N, b), 8.0 * A.numel()),
+                             ("unpack", lambda: st.bcss_unpack(A, out, M, N, b), 8.0 * dense.numel())):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "achieved_gbs": gbs, "algorithmic_bytes": nbytes,
+                     "frac_of_hbm": gbs / float(pk.get("hbm_gbs", 6800.0))}
+    res["bound"] = "hbm"
+    res["peak_gbs"] = float(pk.get("hbm_gbs", 6800.0))
+    res["peak_source"] = "hbm_gbs of %s MEASURED_PEAKS" % pk_src
+    res["bit_exact_round_trip"] = bool(torch.equal(out, dense))
+    del dense, A, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def bcss_pos(j, b):
     import math
     s = sorted(int(x) for x in j)
@@ -885,9 +921,11 @@ def main():
                 "kernel_share_of_step": kern_ms / total_ms if total_ms > 0 else None,
                 "levels": levels}
 
-    e2e = fp64 = rel_err = cpu_base = None
+    e2e = fp64 = rel_err = cpu_base = packbw = None
     C64 = None
     if not args.no_extras:
+        # ---- BCSS pack / unpack of the same tensor (HBM-bound copies)
+        packbw = pack_bandwidth(st, torch, b, pk, pk_src)
         # ---- end to end through the host-buffer entry point
         e2e = end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, max(6, args.steps // 5))
         # ---- plain FP64 GPU path on the same workload (rank 0)
@@ -909,6 +947,7 @@ def main():
                            "useful_flops_per_step": F, "l2": "inputs larger than L2 (A in BCSS FP32: %.0f MB)"
                            % (A.numel() * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e, "fp64_path": fp64, "rel_err": rel_err,
+                "pack_unpack": packbw,
                 "gpu_launches": args.steps * (M + (2 if "tma" in kinds else 1)), "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

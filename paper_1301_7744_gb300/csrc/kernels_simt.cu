@@ -11,58 +11,114 @@ namespace sttsm {
 
 // ------------------------------------------------------------------ pack / unpack
 
-// One CTA per stored block (grid-stride): the block's sorted tuple is
-// unranked once, then the b^m entries are copied with entry e = in-block
-// dimensional offset; consecutive e read consecutive dense addresses.
+// Work unit = (stored block, chunk of PACK_CHUNK in-block entries), grid-
+// stride, so that even few large blocks (b = 64: 364 blocks of 262144
+// entries) keep every SM busy.  The unit's block tuple is unranked once; entry
+// e = in-block dimensional offset, consecutive e read consecutive dense
+// addresses.  The digits of e are taken with 32-bit division when
+// b^m < 2^31 (64-bit otherwise).
+constexpr int64_t PACK_CHUNK = 8192;
+
+template <typename T, typename IT>
+__device__ __forceinline__ void bcss_pack_range(const T* __restrict__ dense, T* __restrict__ dst, const int32_t* tup,
+                                                int m, int64_t n, int b, IT e0, IT e1)
+{
+#pragma unroll 4
+    for (IT e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        IT r = e;
+        int64_t off = 0, stride = 1;
+        bool inside = true;
+        for (int a = 0; a < m; ++a) {
+            const IT q = r / (IT)b;
+            const int64_t i = (int64_t)tup[a] * b + (int64_t)(r - q * (IT)b);
+            r = q;
+            inside = inside && (i < n);
+            off += i * stride;
+            stride *= n;
+        }
+        dst[e] = inside ? dense[off] : T(0);
+    }
+}
+
 template <typename T>
 __global__ void bcss_pack_kernel(const T* __restrict__ dense, T* __restrict__ bcss, int m, int64_t n, int b,
                                  int64_t nblocks, int64_t bm)
 {
     __shared__ int32_t tup[STTSM_MAX_M];
-    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+    const int64_t nchunk = (bm + PACK_CHUNK - 1) / PACK_CHUNK;
+    for (int64_t w = blockIdx.x; w < nblocks * nchunk; w += gridDim.x) {
+        const int64_t blk = w / nchunk, c0 = (w - blk * nchunk) * PACK_CHUNK;
+        const int64_t c1 = c0 + PACK_CHUNK < bm ? c0 + PACK_CHUNK : bm;
         __syncthreads();
         if (threadIdx.x == 0) colex_unrank(blk, m, tup);
         __syncthreads();
         T* dst = bcss + blk * bm;
-        for (int64_t e = threadIdx.x; e < bm; e += blockDim.x) {
-            int64_t r = e, off = 0, stride = 1;
-            bool inside = true;
-            for (int a = 0; a < m; ++a) {
-                int64_t i = (int64_t)tup[a] * b + r % b;
-                r /= b;
-                inside = inside && (i < n);
-                off += i * stride;
-                stride *= n;
-            }
-            dst[e] = inside ? dense[off] : T(0);
-        }
+        if (bm < ((int64_t)1 << 31)) bcss_pack_range<T, uint32_t>(dense, dst, tup, m, n, b, (uint32_t)c0, (uint32_t)c1);
+        else bcss_pack_range<T, int64_t>(dense, dst, tup, m, n, b, c0, c1);
     }
 }
 
-// One thread per dense entry: sort the indices, read the canonical entry.
+// One thread per dense entry: sort the indices (a compare-exchange network on
+// registers), read the canonical entry.  The colex rank of the sorted block
+// tuple sums C(v_t + t, t + 1) over its positions t; with tab the CTA first
+// tabulates those terms for every position and block index in shared memory
+// (m * nbar entries), otherwise each is computed.
 template <typename T>
 __global__ void bcss_unpack_kernel(const T* __restrict__ bcss, T* __restrict__ dense, int m, int64_t n, int b,
-                                   int64_t total, int64_t bm)
+                                   int64_t total, int64_t bm, int nbar, int tab)
 {
+    extern __shared__ int64_t ctab[];   // ctab[t * nbar + v] = C(v + t, t + 1)
+    if (tab) {
+        for (int i = threadIdx.x; i < m * nbar; i += blockDim.x) {
+            const int t = i / nbar, v = i - t * nbar;
+            ctab[i] = binom_small((int64_t)v + t, t + 1);
+        }
+        __syncthreads();
+    }
+    const int64_t rest_total = m > 1 ? total / n : 1;
+    const bool small = rest_total < ((int64_t)1 << 31);
     for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < total;
          lin += (int64_t)gridDim.x * blockDim.x) {
         int32_t s[STTSM_MAX_M];
-        int64_t r = lin;
-        for (int a = 0; a < m; ++a) { s[a] = (int32_t)(r % n); r /= n; }
-        for (int a = 1; a < m; ++a) {  // insertion sort, m <= 8
-            int32_t v = s[a];
-            int c = a - 1;
-            while (c >= 0 && s[c] > v) { s[c + 1] = s[c]; --c; }
-            s[c + 1] = v;
+        const int64_t r0 = lin / n;
+        s[0] = (int32_t)(lin - r0 * n);
+        if (small) {
+            uint32_t r = (uint32_t)r0;
+            const uint32_t un = (uint32_t)n;
+#pragma unroll
+            for (int a = 1; a < STTSM_MAX_M; ++a) {
+                if (a < m) { const uint32_t q = r / un; s[a] = (int32_t)(r - q * un); r = q; }
+            }
+        } else {
+            int64_t r = r0;
+#pragma unroll
+            for (int a = 1; a < STTSM_MAX_M; ++a) {
+                if (a < m) { s[a] = (int32_t)(r % n); r /= n; }
+            }
         }
-        int32_t blk[STTSM_MAX_M];
-        int64_t loc = 0, w = 1;
-        for (int a = 0; a < m; ++a) {
-            blk[a] = s[a] / b;
-            loc += (int64_t)(s[a] % b) * w;
-            w *= b;
+        // bubble network over s[0 .. m-1], fixed indices so s stays in registers
+#pragma unroll
+        for (int i = 0; i < STTSM_MAX_M - 1; ++i) {
+#pragma unroll
+            for (int j = 0; j < STTSM_MAX_M - 1 - i; ++j) {
+                if (j + 1 < m - i) {
+                    const int32_t lo = min(s[j], s[j + 1]), hi = max(s[j], s[j + 1]);
+                    s[j] = lo;
+                    s[j + 1] = hi;
+                }
+            }
         }
-        dense[lin] = bcss[colex_rank(blk, m) * bm + loc];
+        int64_t rank = 0, loc = 0, w = 1;
+#pragma unroll
+        for (int a = 0; a < STTSM_MAX_M; ++a) {
+            if (a < m) {
+                const int32_t v = s[a] / b;
+                rank += tab ? ctab[a * nbar + v] : binom_small((int64_t)v + a, a + 1);
+                loc += (int64_t)(s[a] - v * b) * w;
+                w *= b;
+            }
+        }
+        dense[lin] = bcss[rank * bm + loc];
     }
 }
 
@@ -73,7 +129,8 @@ int launch_bcss_pack(const void* dense, void* bcss, int m, int64_t n, int b, int
     int64_t bm = 1;
     for (int a = 0; a < m; ++a) bm *= b;
     int threads = bm >= 256 ? 256 : (bm >= 64 ? 64 : 32);
-    int64_t g = nblocks < 152 * 64 ? nblocks : 152 * 64;
+    const int64_t work = nblocks * ((bm + PACK_CHUNK - 1) / PACK_CHUNK);
+    int64_t g = work < 152 * 64 ? work : 152 * 64;
     if (dtype == 0) bcss_pack_kernel<double><<<(int)g, threads, 0, s>>>((const double*)dense, (double*)bcss, m, n, b, nblocks, bm);
     else bcss_pack_kernel<float><<<(int)g, threads, 0, s>>>((const float*)dense, (float*)bcss, m, n, b, nblocks, bm);
     return (int)cudaGetLastError();
@@ -83,10 +140,19 @@ int launch_bcss_unpack(const void* bcss, void* dense, int m, int64_t n, int b, i
 {
     int64_t total = 1, bm = 1;
     for (int a = 0; a < m; ++a) { total *= n; bm *= b; }
+    const int64_t nbar = (n + b - 1) / b;
+    // rank terms tabulated in shared memory when they fit in 32 KB
+    const size_t tab_bytes = (size_t)m * (size_t)nbar * sizeof(int64_t);
+    const int tab = tab_bytes <= 32768 ? 1 : 0;
+    const size_t smem = tab ? tab_bytes : 0;
     int64_t g = (total + 255) / 256;
-    if (g > 152 * 64) g = 152 * 64;
-    if (dtype == 0) bcss_unpack_kernel<double><<<(int)g, 256, 0, s>>>((const double*)bcss, (double*)dense, m, n, b, total, bm);
-    else bcss_unpack_kernel<float><<<(int)g, 256, 0, s>>>((const float*)bcss, (float*)dense, m, n, b, total, bm);
+    if (g > 152 * 16) g = 152 * 16;
+    if (dtype == 0)
+        bcss_unpack_kernel<double><<<(int)g, 256, smem, s>>>((const double*)bcss, (double*)dense, m, n, b, total, bm,
+                                                              (int)nbar, tab);
+    else
+        bcss_unpack_kernel<float><<<(int)g, 256, smem, s>>>((const float*)bcss, (float*)dense, m, n, b, total, bm,
+                                                             (int)nbar, tab);
     return (int)cudaGetLastError();
 }
 
