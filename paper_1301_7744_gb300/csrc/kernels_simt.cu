@@ -21,7 +21,7 @@ constexpr int64_t PACK_CHUNK = 8192;
 
 template <typename T, typename IT>
 __device__ __forceinline__ void bcss_pack_range(const T* __restrict__ dense, T* __restrict__ dst, const int32_t* tup,
-                                                int m, int64_t n, int b, IT e0, IT e1)
+                                                int m, int64_t n, int b, int lb, IT e0, IT e1)
 {
 #pragma unroll 4
     for (IT e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -29,7 +29,7 @@ __device__ __forceinline__ void bcss_pack_range(const T* __restrict__ dense, T* 
         int64_t off = 0, stride = 1;
         bool inside = true;
         for (int a = 0; a < m; ++a) {
-            const IT q = r / (IT)b;
+            const IT q = lb >= 0 ? (IT)(r >> lb) : r / (IT)b;   // lb = log2 b when b is a power of two
             const int64_t i = (int64_t)tup[a] * b + (int64_t)(r - q * (IT)b);
             r = q;
             inside = inside && (i < n);
@@ -46,6 +46,7 @@ __global__ void bcss_pack_kernel(const T* __restrict__ dense, T* __restrict__ bc
 {
     __shared__ int32_t tup[STTSM_MAX_M];
     const int64_t nchunk = (bm + PACK_CHUNK - 1) / PACK_CHUNK;
+    const int lb = (b & (b - 1)) == 0 ? __ffs(b) - 1 : -1;
     for (int64_t w = blockIdx.x; w < nblocks * nchunk; w += gridDim.x) {
         const int64_t blk = w / nchunk, c0 = (w - blk * nchunk) * PACK_CHUNK;
         const int64_t c1 = c0 + PACK_CHUNK < bm ? c0 + PACK_CHUNK : bm;
@@ -53,8 +54,8 @@ __global__ void bcss_pack_kernel(const T* __restrict__ dense, T* __restrict__ bc
         if (threadIdx.x == 0) colex_unrank(blk, m, tup);
         __syncthreads();
         T* dst = bcss + blk * bm;
-        if (bm < ((int64_t)1 << 31)) bcss_pack_range<T, uint32_t>(dense, dst, tup, m, n, b, (uint32_t)c0, (uint32_t)c1);
-        else bcss_pack_range<T, int64_t>(dense, dst, tup, m, n, b, c0, c1);
+        if (bm < ((int64_t)1 << 31)) bcss_pack_range<T, uint32_t>(dense, dst, tup, m, n, b, lb, (uint32_t)c0, (uint32_t)c1);
+        else bcss_pack_range<T, int64_t>(dense, dst, tup, m, n, b, lb, c0, c1);
     }
 }
 
@@ -77,11 +78,20 @@ __global__ void bcss_unpack_kernel(const T* __restrict__ bcss, T* __restrict__ d
     }
     const int64_t rest_total = m > 1 ? total / n : 1;
     const bool small = rest_total < ((int64_t)1 << 31);
+    const bool small_lin = total < ((int64_t)1 << 32);
+    const int lb = (b & (b - 1)) == 0 ? __ffs(b) - 1 : -1;
     for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < total;
          lin += (int64_t)gridDim.x * blockDim.x) {
         int32_t s[STTSM_MAX_M];
-        const int64_t r0 = lin / n;
-        s[0] = (int32_t)(lin - r0 * n);
+        int64_t r0;
+        if (small_lin) {
+            const uint32_t l = (uint32_t)lin, q = l / (uint32_t)n;
+            r0 = q;
+            s[0] = (int32_t)(l - q * (uint32_t)n);
+        } else {
+            r0 = lin / n;
+            s[0] = (int32_t)(lin - r0 * n);
+        }
         if (small) {
             uint32_t r = (uint32_t)r0;
             const uint32_t un = (uint32_t)n;
@@ -112,7 +122,7 @@ __global__ void bcss_unpack_kernel(const T* __restrict__ bcss, T* __restrict__ d
 #pragma unroll
         for (int a = 0; a < STTSM_MAX_M; ++a) {
             if (a < m) {
-                const int32_t v = s[a] / b;
+                const int32_t v = lb >= 0 ? (s[a] >> lb) : s[a] / b;
                 rank += tab ? ctab[a * nbar + v] : binom_small((int64_t)v + a, a + 1);
                 loc += (int64_t)(s[a] - v * b) * w;
                 w *= b;
