@@ -100,6 +100,24 @@ def test_workspace_sizes(st):
         st.sttsm_workspace_size(3, 0, 24, 8, st.STTSM_FP64)
 
 
+def test_workspace_covers_the_tma_path(st):
+    """m=3 n=p=768 b=64 BF16X6 runs on the TMA-fed kernel: the workspace must hold
+    the X pieces, A as 3 BF16 pieces per entry and both temporaries as 3 pieces
+    per entry (level 0 writes C(pbar,1) * C(nbar+1,2) blocks, level 1
+    C(pbar+1,2) * nbar blocks of b^3 entries)."""
+    m, n, p, b = 3, 768, 768, 64
+    nbar = pbar = 12
+    bm = b ** m
+    x_pieces = 3 * (pbar * b) * (nbar * b) * 2
+    a_pieces = 3 * math.comb(nbar + 2, 3) * bm * 2
+    t0 = 3 * math.comb(pbar, 1) * math.comb(nbar + 1, 2) * bm * 2
+    t1 = 3 * math.comb(pbar + 1, 2) * nbar * bm * 2
+    ws = st.sttsm_workspace_size(m, n, p, b, st.STTSM_BF16X6)
+    assert ws >= x_pieces + a_pieces + t0 + t1
+    # and not wastefully more (alignment padding only)
+    assert ws <= x_pieces + a_pieces + t0 + t1 + 4 * 256
+
+
 def test_autotune_picks_a_candidate(st):
     for m, n, p in [(3, 20, 12), (4, 64, 40), (5, 33, 33), (3, 768, 768)]:
         cands = (4, 8, 16) if n < 100 else (32, 48, 64)
