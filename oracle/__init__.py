@@ -13,6 +13,7 @@ Functions and what pins them are listed in the header of ``oracle.c``.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -40,12 +41,8 @@ def build(force: bool = False) -> Path:
     return _LIB_PATH
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    build()
-    lib = ctypes.CDLL(str(_LIB_PATH))
+def _bind(lib):
+    """Declares the C signatures on a loaded build of oracle.c."""
     P = ctypes.c_void_p
     i64 = ctypes.c_int64
     lib.oracle_sttsm_bruteforce.argtypes = [ctypes.c_int, i64, i64, P, P, P]
@@ -60,8 +57,30 @@ def _load():
     lib.oracle_bcss_pack.restype = None
     lib.oracle_bcss_flops.argtypes = [ctypes.c_int, i64, i64, ctypes.c_int, ctypes.c_int]
     lib.oracle_bcss_flops.restype = ctypes.c_double
-    _lib = lib
     return lib
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    _lib = _bind(ctypes.CDLL(str(_LIB_PATH)))
+    return _lib
+
+
+@contextlib.contextmanager
+def library(path):
+    """Runs this module's functions on another build of oracle.c (the tests
+    that plant a mistake in a copy of the source use it to show that the pins
+    catch it); the default build is restored afterwards."""
+    global _lib
+    prev = _load()
+    _lib = _bind(ctypes.CDLL(str(path)))
+    try:
+        yield
+    finally:
+        _lib = prev
 
 
 def _f64(a) -> np.ndarray:
