@@ -28,6 +28,8 @@
  *                              storage ratios;
  *   oracle_bcss_flops        — the closed form of Tbl. 4 (MinCosts) and the
  *                              exact b=1 identity derived from Sec. 6.5.
+ * tests/test_oracle_mutations.py plants single mistakes in a copy of this
+ * file and checks that these pins fail on each.
  */
 #include <stdint.h>
 #include <stdlib.h>
