@@ -824,6 +824,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # each rank's GPU is current before any NCCL call (the barrier below runs on it)
+    torch.cuda.set_device(local)
     if rank == 0 or world == 1:
         __graft_entry__.build()
     if world > 1:
@@ -831,7 +833,6 @@ def main():
         dist.barrier()
         if rank != 0:
             __graft_entry__.build()
-    torch.cuda.set_device(local)
     import paper_1301_7744_gb300 as st
 
     prec = st.STTSM_BF16X6 if args.prec == "bf16x6" else st.STTSM_BF16X3
