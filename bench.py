@@ -853,6 +853,11 @@ def main():
         torch.cuda.empty_cache()
     else:
         b = int(args.b)
+    if world > 1:
+        # every replica runs rank 0's block size, so all ranks do the same work
+        tb = torch.tensor([b], device="cuda", dtype=torch.int64)
+        dist.broadcast(tb, 0)
+        b = int(tb.item())
     F = st.sttsm_flops(M, N, P, b)
 
     A = make_device_inputs(st, torch, b, torch.float32)
