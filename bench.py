@@ -348,11 +348,17 @@ def end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, steps):
     for i in range(4):
         e2e_step(i)
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(steps):
         e2e_step(i)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+    if world > 1:
+        e2e_ms = max_over_ranks(e2e_ms, "cuda")   # the slowest replica
     # sequential form (one stream, copies not overlapped) for reference
     t1 = time.perf_counter()
     for i in range(max(2, steps // 4)):
