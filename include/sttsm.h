@@ -123,7 +123,9 @@ int sttsm_workspace_size(int m, int64_t n, int64_t p, int b, int prec, size_t* b
  *   C_bcss: bcss_num_elems(m, p, b) elements, written in full (padding
  *           entries become zero).
  *   workspace: >= sttsm_workspace_size bytes, 256-byte aligned.
- * 1 <= m <= 8; b^{m-1} < 2^31; all pointers 16-byte aligned.  Asynchronous
+ * 1 <= m <= 8; b^{m-1} < 2^31; all pointers 16-byte aligned (a 32-byte
+ * aligned C_bcss lets the last level of the tensor-core path write whole
+ * 32-byte sectors; the result is the same bits either way).  Asynchronous
  * on `stream`.  Returns STTSM_ERR_TIMEOUT if a previous launch on this
  * device recorded a bounded-wait timeout (the status word is then cleared). */
 int sttsm_bcss(const void* A_bcss, const void* X, int m, int64_t n, int64_t p, int b,
