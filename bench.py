@@ -61,6 +61,10 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave the m4 / batch / serve short forms out of the default line")
+    ap.add_argument("--configs-serve-seconds", type=float, default=10.0,
+                    help="length of the serving stream in the default line's short form")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the headline step only (no e2e, FP64 path, check or CPU baseline); for profiling")
     return ap.parse_args()
@@ -74,6 +78,20 @@ def peaks():
         return d, "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def tensor_peak(pk, pk_src, clk, timed_ms):
+    """The BF16 tensor peak that matches a timed region: the burst figure (a cuBLAS
+    GEMM timed alone, at full clock) for a region that is short and saw no power
+    cap, the sustained one (seconds of GEMMs under the power cap) otherwise."""
+    burst = float(pk.get("bf16_tflops", 1900.0))
+    sustained = float(pk.get("bf16_tflops_sustained", 1700.0))
+    capped = "sw_power_cap" in (clk.get("reasons") or [])
+    if timed_ms < 2000.0 and not capped:
+        return burst, ("bf16_tflops (burst) of %s MEASURED_PEAKS: timed region %.0f ms, median SM clock %s MHz, "
+                       "no power cap seen" % (pk_src, timed_ms, clk.get("sm_mhz")))
+    return sustained, ("bf16_tflops_sustained of %s MEASURED_PEAKS: timed region %.0f ms%s"
+                       % (pk_src, timed_ms, ", sw_power_cap seen" if capped else ""))
 
 
 # ---------------------------------------------------------------- clocks
@@ -330,9 +348,14 @@ def profiled_traffic(b, prec, kinds):
 def end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, steps):
     """Same metric through sttsm_bcss_host: every step copies its A and X from
     pinned host buffers to the device, computes, and copies its C back, all inside
-    the timed region.  Steps alternate between two streams with their own device
-    buffers and workspaces (double buffering), so one step's copies overlap the
-    neighbouring steps' computation, as a pipelined caller would run them."""
+    the timed region.  Two forms, each timed over the same number of steps between
+    a barrier and a device synchronisation (slowest rank's time):
+      * "one stream": the steps one after another on one stream;
+      * "two streams": steps alternate between two streams with their own device
+        buffers and workspaces, so one step's copies can overlap the neighbouring
+        steps' computation, as a pipelined caller would run them.
+    The better one is the reported value; the other is kept beside it, with the
+    copy bandwidth of each direction measured alone and both at once."""
     hA = A.cpu().pin_memory()
     hX = torch.from_numpy(xcol32(Xh)).pin_memory()
     hC = [torch.empty(C.numel(), dtype=torch.float32).pin_memory() for _ in range(2)]
@@ -340,38 +363,61 @@ def end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, steps):
     dev = [(torch.empty_like(A), torch.empty(hX.numel(), dtype=torch.float32, device="cuda"), torch.empty_like(C),
             ws if k == 0 else torch.empty_like(ws)) for k in range(2)]
 
-    def e2e_step(i):
-        k = i & 1
+    def step_on(i, k):
         dA2, dX2, dC2, w2 = dev[k]
-        st.sttsm_bcss_host(hA, hX, M, N, P, b, hC[k], prec, dA2, dX2, dC2, w2, streams[k].cuda_stream)
+        st.sttsm_bcss_host(hA, hX, M, N, P, b, hC[i & 1], prec, dA2, dX2, dC2, w2, streams[k].cuda_stream)
 
-    for i in range(4):
-        e2e_step(i)
-    torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    forms = {"two streams": lambda i: step_on(i, i & 1), "one stream": lambda i: step_on(i, 0)}
+
+    def timed(fn, nsteps):
+        for i in range(3):
+            fn(i)
         torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(steps):
-        e2e_step(i)
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
-    if world > 1:
-        e2e_ms = max_over_ranks(e2e_ms, "cuda")   # the slowest replica
-    # sequential form (one stream, copies not overlapped) for reference
-    t1 = time.perf_counter()
-    for i in range(max(2, steps // 4)):
-        st.sttsm_bcss_host(hA, hX, M, N, P, b, hC[0], prec, dev[0][0], dev[0][1], dev[0][2], dev[0][3],
-                           streams[0].cuda_stream)
-        streams[0].synchronize()
-    seq_ms = (time.perf_counter() - t1) * 1e3 / max(2, steps // 4)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(nsteps):
+            fn(i)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / nsteps
+        return max_over_ranks(ms, "cuda") if world > 1 else ms
+
+    res = {name: timed(fn, steps) for name, fn in forms.items()}
     assert np.array_equal(hC[0].numpy(), C.cpu().numpy()) and np.array_equal(hC[1].numpy(), C.cpu().numpy())
-    return {"value": F / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-            "h2d_bytes_per_step": int(hA.numel() * 4 + hX.numel() * 4), "d2h_bytes_per_step": int(hC[0].numel() * 4),
-            "timer": "host wall clock over the steps, device synchronised at both ends",
-            "pipelining": "2 streams, double-buffered device buffers; each step's own H2D, compute and D2H",
-            "sequential_ms_per_step": seq_ms, "steps": steps}
+    # copy bandwidth alone: H2D of A, D2H of C, and both directions at once (two streams)
+    h2d_bytes, d2h_bytes = hA.numel() * 4, hC[0].numel() * 4
+
+    def copy_ms(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / reps
+
+    def both():
+        with torch.cuda.stream(streams[0]):
+            dev[0][0].copy_(hA, non_blocking=True)
+        with torch.cuda.stream(streams[1]):
+            hC[1].copy_(dev[1][2], non_blocking=True)
+
+    t_h2d = copy_ms(lambda: dev[0][0].copy_(hA, non_blocking=True))
+    t_d2h = copy_ms(lambda: hC[0].copy_(dev[0][2], non_blocking=True))
+    t_both = copy_ms(both)
+    best = min(res, key=res.get)
+    ms = res[best]
+    return {"value": F / (ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "ms_per_step": ms, "form": best,
+            "ms_per_step_by_form": res,
+            "value_by_form": {k: F / (v * 1e-3) / 1e12 * world for k, v in res.items()},
+            "h2d_bytes_per_step": int(h2d_bytes + hX.numel() * 4), "d2h_bytes_per_step": int(d2h_bytes),
+            "timer": "host wall clock over the steps, barrier and device synchronisation at both ends, max over ranks",
+            "copy_gbs": {"h2d_alone": h2d_bytes / (t_h2d * 1e-3) / 1e9, "d2h_alone": d2h_bytes / (t_d2h * 1e-3) / 1e9,
+                         "h2d_and_d2h_at_once": (h2d_bytes + d2h_bytes) / (t_both * 1e-3) / 1e9,
+                         "what": "pinned host <-> device copies of the workload's A (H2D) and C (D2H), 5 reps each"},
+            "steps": steps}
 
 
 def fp64_path(st, torch, Xh, b, F, ms):
@@ -406,12 +452,14 @@ def check_and_baseline(args, C, C64, Xh, X32, b, F, world):
     c32 = C.double().cpu().numpy()
     got32 = np.array([c32[bcss_pos(j, b)] for j in J])
     rel_err = {"samples": 256, args.prec: float(np.linalg.norm(got32 - ref32) / np.linalg.norm(ref32)),
-               "tolerance": {args.prec: 1e-6, "fp64": 1e-12}}
+               "tolerance": {args.prec: 1e-6, "fp64": 1e-12},
+               "elementwise": {args.prec: float(np.max(np.abs(got32 - ref32)) / np.max(np.abs(ref32)))}}
     if C64 is not None:
         ref64 = oracle.sttsm_entries(A_dense, Xh, M, J)
         c64 = C64.cpu().numpy()
         got64 = np.array([c64[bcss_pos(j, b)] for j in J])
         rel_err["fp64"] = float(np.linalg.norm(got64 - ref64) / np.linalg.norm(ref64))
+        rel_err["elementwise"]["fp64"] = float(np.max(np.abs(got64 - ref64)) / np.max(np.abs(ref64)))
     cpu_base = None
     if world == 1:
         dt, S = oracle_slice_rate(A_dense, X32, args.cpu_seconds)
@@ -450,10 +498,11 @@ def bcss_pos_m(j, b, m):
     return rank * b ** m + sum((s[t] % b) * b ** t for t in range(m))
 
 
-def run_m4(args):
+def run_m4(args, emit=True, short=False):
     """The compressing single instance m = 4, n = 128, p = 64 (X with orthonormal
     rows), b in {8, 16, 32}, BF16X6 and FP64: TFLOP/s per (b, precision) and the
-    error of 64 sampled C entries against the FP64 oracle."""
+    error of 64 sampled C entries against the FP64 oracle.  short: at most 10
+    timed steps per case (the form the default bench line carries)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -464,8 +513,10 @@ def run_m4(args):
     stream = torch.cuda.current_stream().cuda_stream
     Xh = synth.x_orthonormal_rows(SEED_X, p, n)
     X32 = Xh.astype(np.float32).astype(np.float64)
-    steps, warm = max(3, min(args.steps, 50)), max(3, args.warmup)
+    steps, warm = max(3, min(args.steps, 10 if short else 50)), max(3, args.warmup)
     res, keep = {}, {}
+    clocks = ClockSampler()
+    clocks.start()
     for b in (8, 16, 32):
         for prec, name, dt in ((st.STTSM_BF16X6, "bf16x6", torch.float32), (st.STTSM_FP64, "fp64", torch.float64)):
             dense = torch.empty(n ** m, dtype=dt, device="cuda")
@@ -489,6 +540,7 @@ def run_m4(args):
             keep[(name, b)] = C.double().cpu().numpy()
             del A, C, ws, X
             torch.cuda.empty_cache()
+    clk = clocks.stop()
     oracle.build()
     A_dense = synth.sym_uniform_dense(m, n, SEED_A)
     J = np.sort(np.random.default_rng(SEED_J).integers(0, p, size=(64, m)), axis=1)
@@ -497,14 +549,19 @@ def run_m4(args):
         got = np.array([c[bcss_pos_m(j, b, m)] for j in J])
         res["%s_b%d" % (name, b)]["rel_err"] = float(np.linalg.norm(got - ref[name]) / np.linalg.norm(ref[name]))
     best = max((k for k in res if k.startswith("bf16x6")), key=lambda k: res[k]["tflops"])
+    fastest = min((k for k in res if k.startswith("bf16x6")), key=lambda k: res[k]["ms_per_step"])
     line = {"metric": "sttsm TFLOP/s, m=4 n=128 p=64 (compressing)", "value": res[best]["tflops"], "unit": "TFLOP/s",
             "n_gpus": 1, "steps": steps, "warmup": warm, "higher_is_better": True, "dtype": "bf16x6",
             "data": "synthetic", "config": {"workload": "sttsm m=4 n=128 p=64, X orthonormal rows, b in {8,16,32}",
                                             "best": best, "tolerance": {"bf16x6": 1e-6, "fp64": 1e-12},
                                             "oracle_samples": 64},
-            "results": res}
-    print(json.dumps(line), flush=True)
-    return 0
+            "time_to_solution": {"case": fastest, "ms_per_step": res[fastest]["ms_per_step"],
+                                 "tflops": res[fastest]["tflops"]},
+            "results": res, "clocks": clk}
+    if emit:
+        print(json.dumps(line), flush=True)
+        return 0
+    return line
 
 
 def run_abo(args):
@@ -559,11 +616,12 @@ def run_abo(args):
     return 0
 
 
-def run_batch(args):
+def run_batch(args, emit=True, short=False):
     """Batched workload: count instances, m in {3,4,5} (weights .5/.3/.2), n in U{8..64},
     p in U{8..n}, b per instance by sttsm_autotune_b over {4, 8, 16}; BF16X6; one
     sttsm_batch_run (a CUDA-graph replay) per step.  Compared with a per-instance loop
-    of the plain FP64 path (sttsm_bcss per instance)."""
+    of the plain FP64 path (sttsm_bcss per instance).  short: no FP64 loop and no
+    tcgen05 comparison (the form the default bench line carries)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -603,7 +661,7 @@ def run_batch(args):
     capture_s = time.perf_counter() - t0
     steps = max(3, min(args.steps, 20))
     tot_tc = None
-    if not args.no_extras:
+    if not args.no_extras and not short:
         # the tcgen05 small-tile kernel for the same plan (for comparison)
         st.sttsm_set_small_kernel(st.SMALL_TCGEN05)
         plan_tc = st.BatchPlan(insts, prec, ws_budget=int(args.ws_gb * 2 ** 30))
@@ -624,7 +682,7 @@ def run_batch(args):
     # accuracy on a sample of instances against the oracle
     import oracle
     rng = np.random.default_rng(0)
-    errs = []
+    errs, errs_el = [], []
     small = [i for i, (m, n, p) in enumerate(shapes) if n ** m <= 2e7]
     for i in rng.choice(small, size=min(16, len(small)), replace=False):
         A_, dX_, C_, m, n, p, b = insts[i]
@@ -633,25 +691,29 @@ def run_batch(args):
         ref = oracle.bcss_pack(oracle.sttsm_chain(Ad, X32, m), m, p, b)
         got = C_.double().cpu().numpy()
         errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
-    # the per-instance loop of the plain FP64 path
-    scratch64 = torch.empty(maxdense, dtype=torch.float64, device="cuda")
-    f64 = []
-    for i, (A_, dX_, C_, m, n, p, b) in enumerate(insts):
-        d = scratch64[: n ** m]
-        synth.dev_sym_uniform_dense(d.data_ptr(), m, n, 1000 + i, "f64", stream)
-        A64 = torch.empty(st.bcss_num_elems(m, n, b), dtype=torch.float64, device="cuda")
-        st.bcss_pack(d, A64, m, n, b)
-        X64 = torch.from_numpy(np.asfortranarray(xs[i]).reshape(-1, order="F").copy()).cuda()
-        C64 = torch.empty(st.bcss_num_elems(m, p, b), dtype=torch.float64, device="cuda")
-        f64.append((A64, X64, C64, m, n, p, b, st.workspace_tensor(m, n, p, b, st.STTSM_FP64)))
-    del scratch64
-    torch.cuda.synchronize()
+        errs_el.append(float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+    tot64 = None
+    if not short:
+        # the per-instance loop of the plain FP64 path
+        scratch64 = torch.empty(maxdense, dtype=torch.float64, device="cuda")
+        f64 = []
+        for i, (A_, dX_, C_, m, n, p, b) in enumerate(insts):
+            d = scratch64[: n ** m]
+            synth.dev_sym_uniform_dense(d.data_ptr(), m, n, 1000 + i, "f64", stream)
+            A64 = torch.empty(st.bcss_num_elems(m, n, b), dtype=torch.float64, device="cuda")
+            st.bcss_pack(d, A64, m, n, b)
+            X64 = torch.from_numpy(np.asfortranarray(xs[i]).reshape(-1, order="F").copy()).cuda()
+            C64 = torch.empty(st.bcss_num_elems(m, p, b), dtype=torch.float64, device="cuda")
+            f64.append((A64, X64, C64, m, n, p, b, st.workspace_tensor(m, n, p, b, st.STTSM_FP64)))
+        del scratch64
+        torch.cuda.synchronize()
 
-    def loop64():
-        for (A64, X64, C64, m, n, p, b, w64) in f64:
-            st.sttsm_bcss(A64, X64, m, n, p, b, C64, st.STTSM_FP64, w64)
+        def loop64():
+            for (A64, X64, C64, m, n, p, b, w64) in f64:
+                st.sttsm_bcss(A64, X64, m, n, p, b, C64, st.STTSM_FP64, w64)
 
-    tot64, _ = time_steps(torch, loop64, 1, 1)
+        tot64, _ = time_steps(torch, loop64, 1, 1)
+        del f64
     # executed FMAs of the small-contraction kernel (tile rows x compile-time column
     # width x contraction padded to 4) and the algorithmic bytes (parents read, outputs
     # written, FP32) of every level of every instance, from the library's own plans
@@ -676,7 +738,7 @@ def run_batch(args):
                        "waves": info["waves"], "workspace_gb": plan.workspace_size() / 2 ** 30,
                        "plan_seconds": plan_s, "graph_capture_seconds": capture_s},
             "fp64_per_instance_loop": {"value": F / (tot64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms": tot64,
-                                       "speedup_of_batch": tot64 / ms},
+                                       "speedup_of_batch": tot64 / ms} if tot64 else None,
             "small_kernel": "fp32 cuda-core (n̄b <= 64 contractions)",
             "median_ms_per_step": float(np.median(per)),
             "roofline": {"bound": "alu", "achieved": exec_flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
@@ -692,17 +754,19 @@ def run_batch(args):
             "tcgen05_small_tile_kernel": {"value": F / (tot_tc / 3 * 1e-3) / 1e12, "unit": "TFLOP/s",
                                           "ms_per_step": tot_tc / 3} if tot_tc else None,
             "rel_err": {"instances_checked": len(errs), "max": max(errs), "median": float(np.median(errs)),
-                        "tolerance": 1e-6},
+                        "max_elementwise": max(errs_el), "tolerance": 1e-6},
             "clocks": clk}
-    print(json.dumps(line), flush=True)
     plan.destroy()
-    return 0
+    if emit:
+        print(json.dumps(line), flush=True)
+        return 0
+    return line
 
 
 SERVE_B = {3: (16, 32, 64), 4: (8, 16, 32), 5: (4, 8, 16), 6: (4, 8)}
 
 
-def run_serve(args):
+def run_serve(args, emit=True, seconds=None):
     """Serving workload: Poisson arrivals (rate, seconds), uniform over the classes
     m=3 (n,p in [64,512]), m=4 ([32,160]), m=5 ([16,64]), m=6 ([8,32]); BF16X6; the
     server admits by HBM budget and batches continuously.  Inputs come from a pool of
@@ -714,7 +778,8 @@ def run_serve(args):
     import paper_1301_7744_gb300 as st
     import synth
     prec = st.STTSM_BF16X6
-    reqs = synth.serve_requests(4, args.serve_rate, args.serve_seconds)
+    seconds = float(seconds or args.serve_seconds)
+    reqs = synth.serve_requests(4, args.serve_rate, seconds)
     pool_n, cbuf = 32, 8
     rng = np.random.default_rng(11)
     stream = torch.cuda.current_stream().cuda_stream
@@ -744,6 +809,7 @@ def run_serve(args):
     while not all(srv.poll(t)[0] for t in warm):
         time.sleep(0.001)
     count = {m: 0 for m in pool}
+    used = set()
     tickets, flops = [], 0.0
     busy = 0
     clocks = ClockSampler()
@@ -759,6 +825,7 @@ def run_serve(args):
                 time.sleep(dt - 1e-4)
         e = pool[m][count[m] % pool_n]
         c = e["C"][(count[m] // pool_n) % cbuf]
+        used.add((m, count[m] % pool_n, (count[m] // pool_n) % cbuf))
         count[m] += 1
         while True:
             try:
@@ -793,8 +860,25 @@ def run_serve(args):
     clk = clocks.stop()
     srv.destroy()
     lat = np.array(lat)
+    # accuracy: per class the two pool entries with the smallest dense sizes, every C
+    # buffer a request wrote, all stored entries against the oracle's dense chain
+    import oracle
+    oracle.build()
+    errs = []
+    for m in pool:
+        small = sorted(range(pool_n), key=lambda k: max(pool[m][k]["n"], pool[m][k]["p"]))[:2]
+        for k in small:
+            E = pool[m][k]
+            n, p, b = E["n"], E["p"], E["b"]
+            Ad = synth.sym_uniform_dense(m, n, 7000 + 100 * m + k)
+            X32 = synth.x_gaussian(8000 + 100 * m + k, p, n).astype(np.float32).astype(np.float64)
+            ref = oracle.bcss_pack(oracle.sttsm_chain(Ad, X32, m), m, p, b)
+            for j in sorted({0} | {u[2] for u in used if u[0] == m and u[1] == k}):
+                got = E["C"][j].double().cpu().numpy()
+                errs.append((float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                             float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))))
     line = {"metric": "sttsm serving latency p50/p99 (ms) and throughput, Poisson %.0f req/s for %.0f s"
-                      % (args.serve_rate, args.serve_seconds),
+                      % (args.serve_rate, seconds),
             "value": float(np.percentile(lat, 99)), "unit": "ms (p99 latency)", "higher_is_better": False,
             "n_gpus": 1, "dtype": "bf16x6", "data": "synthetic",
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -802,13 +886,19 @@ def run_serve(args):
             "requests": len(lat), "throughput_req_s": len(lat) / wall, "useful_tflops": flops / wall / 1e12,
             "submit_seconds": t_sub, "wall_seconds": wall, "busy_retries": busy,
             "max_queued": max_queue, "max_active": max_active, "max_arena_gb": max_arena / 2 ** 30,
+            "rel_err": {"outputs_checked": len(errs), "max_fro": max(e[0] for e in errs),
+                        "max_elementwise": max(e[1] for e in errs), "tolerance": 1e-6,
+                        "what": "full C of the two smallest pool entries per class vs the FP64 oracle's dense chain; "
+                                "elementwise = max |C - C_oracle| / max |C_oracle|"},
             "config": {"workload": "Poisson stream, classes m=3 n,p in [64,512]; m=4 [32,160]; m=5 [16,64]; "
                                    "m=6 [8,32]; b autotuned per pool entry",
                        "hbm_budget_gb": args.serve_budget_gb, "pool_per_class": pool_n,
                        "b_candidates": {str(k): v for k, v in SERVE_B.items()}},
             "clocks": clk}
-    print(json.dumps(line), flush=True)
-    return 0
+    if emit:
+        print(json.dumps(line), flush=True)
+        return 0
+    return line
 
 
 def main():
@@ -900,7 +990,7 @@ def main():
     nprod = 6 if prec == st.STTSM_BF16X6 else 3
     pk, pk_src = peaks()
     mma_tflops = kern_flops * nprod / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else 0.0
-    peak = float(pk.get("bf16_tflops_sustained", 1700.0))
+    peak, peak_source = tensor_peak(pk, pk_src, clk, total_ms)
     per_level = {}
     for r in tc:
         d = per_level.setdefault(r["level"], {"ms": 0.0, "flops": 0.0, "n": 0})
@@ -928,7 +1018,8 @@ def main():
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": {"tma": "level_tma_kernel", "tc": "level_tc_kernel"}[kinds[0]] + " (all m levels)" if kinds else None,
                 "achieved_counts": "useful flops x %d piece products per launch / CUDA-event duration" % nprod,
-                "peak_source": "bf16_tflops_sustained of %s MEASURED_PEAKS" % pk_src,
+                "peak_source": peak_source,
+                "frac_of_sustained_peak": mma_tflops / float(pk.get("bf16_tflops_sustained", 1700.0)),
                 "useful_tflops": kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else 0.0,
                 "kernel_share_of_step": kern_ms / total_ms if total_ms > 0 else None,
                 "levels": levels}
@@ -939,13 +1030,37 @@ def main():
         # ---- BCSS pack / unpack of the same tensor (HBM-bound copies)
         packbw = pack_bandwidth(st, torch, b, pk, pk_src)
         # ---- end to end through the host-buffer entry point
-        e2e = end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, max(6, args.steps // 5))
+        e2e = end_to_end(st, torch, A, C, Xh, ws, b, F, prec, world, max(20, args.steps))
         # ---- plain FP64 GPU path on the same workload (rank 0)
         if rank == 0:
             fp64, C64 = fp64_path(st, torch, Xh, b, F, ms)
         # ---- accuracy against the oracle and the CPU baseline (rank 0; baseline at N = 1)
         if rank == 0 and not args.no_check:
             rel_err, cpu_base = check_and_baseline(args, C, C64, Xh, X32, b, F, world)
+
+    # ---- the other configurations, short forms (N = 1 only): m=4 n=128 p=64, the
+    # 4096-instance batch, the serving stream
+    configs = None
+    a_mb = A.numel() * 4 / 1e6
+    if world == 1 and not args.no_extras and not args.no_configs:
+        del A, C, ws, C64
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        configs = {}
+        for name, fn in (("m4", lambda: run_m4(args, emit=False, short=True)),
+                         ("batch", lambda: run_batch(args, emit=False, short=True)),
+                         ("serve", lambda: run_serve(args, emit=False, seconds=args.configs_serve_seconds))):
+            t0 = time.perf_counter()
+            configs[name] = fn()
+            configs[name]["wall_seconds_of_leg"] = time.perf_counter() - t0
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+
+    tts = None
+    if sweep:
+        ms_fast = times[b_fastest]
+        tts = {"b": b_fastest, "ms_per_step": ms_fast, "tflops": st.sttsm_flops(M, N, P, b_fastest) / (ms_fast * 1e-3) / 1e12,
+               "headline_b_ms_per_step": times.get(b), "source": "median of the autotuner's timed runs per b"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -957,9 +1072,10 @@ def main():
                            "b": b, "precision": args.prec, "b_sweep_tflops": {str(k): v for k, v in sweep.items()},
                            "b_fastest_by_time": b_fastest,
                            "useful_flops_per_step": F, "l2": "inputs larger than L2 (A in BCSS FP32: %.0f MB)"
-                           % (A.numel() * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},
+                           % a_mb, "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e, "fp64_path": fp64, "rel_err": rel_err,
                 "pack_unpack": packbw,
+                "time_to_solution": tts, "configs": configs,
                 "gpu_launches": args.steps * (M + (2 if "tma" in kinds else 1)), "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -265,16 +265,36 @@ int sttsm_serve_destroy(void* handle);
  *   (m = 3, n = p = 128, b = 32 fits; use sttsm_bcss with a caller
  *   workspace beyond that).
  *   Set-up: the first call on each device looks up the array's device
- *   address (cudaGetSymbolAddress) and zeroes its status word; make that
- *   first call before any stream capture.
+ *   address (cudaGetSymbolAddress) and page-locks and maps a static host
+ *   status word for that device (cudaHostRegister: no allocation); make
+ *   that first call before any stream capture.
+ *   Errors: a bounded wait that runs out in this entry point's kernels
+ *   raises its status word; the next sttsm_bcss_noalloc call on that device
+ *   returns STTSM_ERR_TIMEOUT before launching anything and clears it (the C
+ *   of the call that timed out is undefined).  sttsm_device_status does not
+ *   see this word.
+ *   Plans: the level plans of the last shape (m, n, p, b, prec) stay in the
+ *   array; a call with another shape rebuilds them on the host and copies
+ *   them in on `stream`.  That copy is refused with STTSM_ERR_UNSUPPORTED
+ *   while `stream` is capturing.  Work already enqueued or recorded for the
+ *   earlier shape must not run after a call with another shape.
  *   Sharing: every call uses the same array and finds the previous call's
  *   contents there.  Calls that overlap on the GPU (several streams or host
- *   threads) race on it and corrupt each other: serialise them.  Device-side
- *   wait timeouts are recorded in the array, not in sttsm_device_status.
+ *   threads) race on it and corrupt each other: serialise them.
  * Arguments, layouts and results are those of sttsm_bcss. */
 #define STTSM_NOALLOC_SCRATCH_BYTES (64u << 20)
 int sttsm_bcss_noalloc(const void* A_bcss, const void* X, int m, int64_t n, int64_t p, int b,
                        void* C_bcss, int prec, void* stream);
+
+/* Self-test of the failure path of sttsm_bcss_noalloc: sets that entry
+ * point up on the current device if needed, launches one kernel whose
+ * thread waits on an mbarrier nothing arrives on, bounded by limit_ms
+ * (0 < limit_ms <= 1000), through the bounded wait the level kernels use,
+ * and synchronises the device.  The wait runs out and raises the entry
+ * point's status word, which the next sttsm_bcss_noalloc call reports as
+ * STTSM_ERR_TIMEOUT.  Returns STTSM_OK, or STTSM_ERR_ARG for an
+ * out-of-range limit. */
+int sttsm_noalloc_selftest_wait_timeout(double limit_ms);
 
 /* Kernel for short contractions (n̄ b <= 64) under the split precisions:
  * 0 (default) = FP32 FMAs on the CUDA cores, one thread per output row (at

@@ -119,6 +119,8 @@ def _load():
     L.sttsm_set_small_kernel.restype = i32
     L.sttsm_bcss_noalloc.argtypes = [P, P, i32, i64, i64, i32, P, i32, P]
     L.sttsm_bcss_noalloc.restype = i32
+    L.sttsm_noalloc_selftest_wait_timeout.argtypes = [ctypes.c_double]
+    L.sttsm_noalloc_selftest_wait_timeout.restype = i32
     L.sttsm_profile_enable.argtypes = [i32]
     L.sttsm_profile_enable.restype = i32
     L.sttsm_profile_read.argtypes = [i32, P, P, P, P, P]
@@ -137,7 +139,7 @@ def exported_symbols() -> list[str]:
             "sttsm_autotune_b_measured", "sttsm_batch_plan_create", "sttsm_batch_workspace_size",
             "sttsm_batch_info", "sttsm_batch_run", "sttsm_batch_plan_destroy", "sttsm_batch", "sttsm_serve_create",
             "sttsm_serve_submit", "sttsm_serve_poll", "sttsm_serve_stats", "sttsm_serve_destroy",
-            "sttsm_bcss_noalloc", "sttsm_set_small_kernel", "sttsm_device_status", "sttsm_selftest_wait_timeout",
+            "sttsm_bcss_noalloc", "sttsm_noalloc_selftest_wait_timeout", "sttsm_set_small_kernel", "sttsm_device_status", "sttsm_selftest_wait_timeout",
             "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read"]
 
 
@@ -284,6 +286,12 @@ def sttsm_bcss_noalloc(A, X, m: int, n: int, p: int, b: int, C, prec: int, strea
     _check_operands(A, X, C, m, n, p, b, prec)
     _check("sttsm_bcss_noalloc", _load().sttsm_bcss_noalloc(_dptr(A), _dptr(X), m, n, p, b, _dptr(C), prec,
                                                             _stream(stream)))
+
+
+def sttsm_noalloc_selftest_wait_timeout(limit_ms: float) -> None:
+    """Runs the bounded-wait self-test on sttsm_bcss_noalloc's status word; the next
+    sttsm_bcss_noalloc call on this device then reports STTSM_ERR_TIMEOUT."""
+    _check("sttsm_noalloc_selftest_wait_timeout", _load().sttsm_noalloc_selftest_wait_timeout(float(limit_ms)))
 
 
 def sttsm_bcss_host(A, X, m: int, n: int, p: int, b: int, C, prec: int, dA, dX, dC, workspace, stream=None) -> None:

@@ -27,6 +27,14 @@ def rel_fro(got, ref):
     return float(np.linalg.norm(np.asarray(got) - np.asarray(ref)) / np.linalg.norm(ref))
 
 
+def rel_max(got, ref):
+    """Elementwise bound beside the Frobenius one: max |got - ref| / max |ref|
+    (a wrong block among many right ones shows here even where a norm over all
+    entries would hide it)."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
 def device_bcss_from_dense(st, dense_np, m, n, b, dtype):
     import torch
     d = torch.from_numpy(np.ascontiguousarray(dense_np)).to(device="cuda", dtype=dtype)

@@ -166,3 +166,22 @@ def test_measured_autotune_rejects_bad_arguments_on_the_host(st):
     assert f(3, 100, 100, st.STTSM_BF16X6, c.ctypes.data, 0, 3, None) == st.STTSM_ERR_ARG
     assert f(3, 100, 100, st.STTSM_BF16X6, c.ctypes.data, 2, 0, None) == st.STTSM_ERR_ARG
     assert f(3, 100, 100, st.STTSM_TF32X3, c.ctypes.data, 2, 3, None) == st.STTSM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("m,n,p,b", [(3, 24, 24, 8), (3, 768, 768, 64), (3, 768, 768, 32), (3, 768, 768, 48),
+                                     (4, 128, 64, 8), (4, 128, 64, 16), (4, 128, 64, 32), (5, 37, 20, 4),
+                                     (2, 9, 11, 3), (1, 10, 7, 4), (6, 20, 12, 8), (3, 320, 320, 32)])
+@pytest.mark.parametrize("precname", ["fp64", "bf16x6"])
+def test_work_list_issues_the_table4_count(st, m, n, p, b, precname):
+    """The multiply-adds the emitted tiles cover (valid rows x columns x n̄ b, times
+    2), summed over every tile of every level, equal the oracle's loop-counted
+    Tbl. 4 flop count exactly: the work list neither drops nor repeats work."""
+    prec = st.STTSM_FP64 if precname == "fp64" else st.STTSM_BF16X6
+    nbar = -(-n // b)
+    total = 0
+    for d in range(m):
+        tiles, _, info = st.sttsm_plan_level(m, n, p, b, prec, d)
+        rows = np.minimum(info["BM"], info["rows_per_parent"] - tiles[:, 3].astype(np.int64))
+        assert (rows > 0).all()
+        total += int(2 * (rows * tiles[:, 5].astype(np.int64)).sum()) * nbar * b
+    assert total == int(oracle.bcss_flops(m, n, p, b))

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import bcss_pos, device_bcss_from_dense, inputs, oracle_C_bcss, rel_fro, run_sttsm, xcol
+from helpers import bcss_pos, device_bcss_from_dense, inputs, oracle_C_bcss, rel_fro, rel_max, run_sttsm, xcol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -137,6 +137,47 @@ def test_shapes(st, m, n, p, b, precname):
     ref = oracle_C_bcss(A, X, m, p, b)
     assert not np.isnan(got).any()
     assert rel_fro(got, ref) <= TOL[precname]
+    assert rel_max(got, ref) <= TOL[precname]
+
+
+# Parents wider than 256 output columns: the balanced column split (several
+# tiles per parent), X boxes of several heights, and p > n; every C entry is
+# checked against the oracle's dense chain.
+WIDE = {(3, 320, 320): (32,), (3, 384, 384): (64, 48), (3, 256, 384): (64, 32)}
+
+
+@pytest.fixture(scope="module")
+def wide_refs():
+    cache = {}
+
+    def get(m, n, p, precname):
+        key = (m, n, p, precname)
+        if key not in cache:
+            A, X = inputs(m, n, p, seed_a=11, seed_x=12, fp32=precname != "fp64")
+            cache[key] = (A, X, oracle.sttsm_chain(A, X, m))
+        return cache[key]
+    return get
+
+
+@pytest.mark.parametrize("m,n,p,b", [(m, n, p, b) for (m, n, p), bs in WIDE.items() for b in bs])
+def test_wide_parents_full_C(st, wide_refs, m, n, p, b):
+    A, X, Cd = wide_refs(m, n, p, "bf16x6")
+    Ab = device_bcss_from_dense(st, A, m, n, b, torch.float32)
+    got = run_sttsm(st, Ab, X, m, n, p, b, st.STTSM_BF16X6)
+    ref = oracle.bcss_pack(Cd, m, p, b)
+    ef, em = rel_fro(got, ref), rel_max(got, ref)
+    print("wide m=%d n=%d p=%d b=%d: rel fro %.3e, elementwise %.3e" % (m, n, p, b, ef, em))
+    assert not np.isnan(got).any()
+    assert ef <= TOL["bf16x6"] and em <= TOL["bf16x6"]
+
+
+def test_wide_parents_full_C_fp64(st, wide_refs):
+    m, n, p, b = 3, 256, 384, 64
+    A, X, Cd = wide_refs(m, n, p, "fp64")
+    Ab = device_bcss_from_dense(st, A, m, n, b, torch.float64)
+    got = run_sttsm(st, Ab, X, m, n, p, b, st.STTSM_FP64)
+    ref = oracle.bcss_pack(Cd, m, p, b)
+    assert rel_fro(got, ref) <= TOL["fp64"] and rel_max(got, ref) <= TOL["fp64"]
 
 
 @pytest.mark.parametrize("m,n,p,b", [(3, 100, 90, 16), (4, 70, 40, 16), (3, 96, 96, 32)])
@@ -208,9 +249,11 @@ def test_config3(st, config3, b, precname):
     Cref = c["C64"] if precname == "fp64" else c["C32"]
     Ab = device_bcss_from_dense(st, c["A"], m, n, b, dtype_of(precname))
     got = run_sttsm(st, Ab, X, m, n, p, b, prec_of(st, precname))
-    err = rel_fro(got, oracle.bcss_pack(Cref, m, p, b))
-    print("config3 b=%d %s rel err %.3e" % (b, precname, err))
+    ref = oracle.bcss_pack(Cref, m, p, b)
+    err = rel_fro(got, ref)
+    print("config3 b=%d %s rel err %.3e, elementwise %.3e" % (b, precname, err, rel_max(got, ref)))
     assert err <= TOL[precname]
+    assert rel_max(got, ref) <= TOL[precname]
 
 
 def test_config3_rank8_closed_form(st):
@@ -263,8 +306,9 @@ def test_config2_sampled(st, config2, b, precname):
     vals = np.array([got[bcss_pos(j, m, b)] for j in c["J"]])
     ref = c["ref64"] if precname == "fp64" else c["ref32"]
     err = rel_fro(vals, ref)
-    print("config2 b=%d %s sampled rel err %.3e" % (b, precname, err))
+    print("config2 b=%d %s sampled rel err %.3e, elementwise %.3e" % (b, precname, err, rel_max(vals, ref)))
     assert err <= TOL[precname]
+    assert rel_max(vals, ref) <= TOL[precname]
     assert not np.isnan(got).any()
 
 
