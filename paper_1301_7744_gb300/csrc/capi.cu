@@ -156,8 +156,8 @@ int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, i
     for (int a = 0; a < m - 1; ++a) R *= b;
     const int64_t bm = R * b;
     int64_t bq = 1;
-    if (b == 16) {
-        // one stored block per 16-wide K slice, 32-byte swizzle
+    if (tma_sw32_b(b)) {
+        // one box per 16-wide K slice, 32-byte swizzle
         for (int q = 0; q <= k; ++q, bq *= b) {
             CUresult r;
             if (q == 0) {
@@ -170,12 +170,15 @@ int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, i
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             } else {
-                // MN-major: {16 rows (contiguous), a (b^q apart), 16-row atoms, outer rows (b^(q+1) apart), block x piece}
+                // MN-major: {16 rows (contiguous), a (b^q apart), 16-row atoms, outer rows (b^(q+1) apart), block x piece};
+                // a run of b^q rows that neither divides 128 nor is a multiple of it is
+                // loaded one 16-row atom per box (the kernel's atom-by-atom layout)
+                const bool atomwise = (bq % 128) != 0 && (128 % bq) != 0;
                 cuuint64_t dims[5] = {16, (cuuint64_t)b, (cuuint64_t)(bq / 16), (cuuint64_t)(R / bq),
                                       (cuuint64_t)(nblocks * npiece)};
                 cuuint64_t strides[4] = {(cuuint64_t)bq * 2, 32, (cuuint64_t)bq * b * 2, (cuuint64_t)bm * 2};
-                cuuint32_t box[5] = {16, 16, (cuuint32_t)((bq < 128 ? bq : 128) / 16), (cuuint32_t)(bq < 128 ? 128 / bq : 1),
-                                     (cuuint32_t)npiece};
+                cuuint32_t box[5] = {16, 16, atomwise ? 1u : (cuuint32_t)((bq < 128 ? bq : 128) / 16),
+                                     atomwise ? 1u : (cuuint32_t)(bq < 128 ? 128 / bq : 1), (cuuint32_t)npiece};
                 cuuint32_t estr[5] = {1, 1, 1, 1, 1};
                 r = enc(&maps[q], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(pieces), dims, strides, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -462,7 +465,7 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
             for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
             const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
             ProfScope ps(stream, 3, d, lflops);
-            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d < nlev - 1 ? TMA_OUT_PIECES : (d == m - 1 ? TMA_OUT_C : TMA_OUT_F32), b == 16, P->maxcols[d], stream));
+            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d < nlev - 1 ? TMA_OUT_PIECES : (d == m - 1 ? TMA_OUT_C : TMA_OUT_F32), tma_sw32(s), P->maxcols[d], stream));
             if (rc != STTSM_OK) return rc;
         }
         return STTSM_OK;

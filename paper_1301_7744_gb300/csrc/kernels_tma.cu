@@ -1,17 +1,21 @@
 // kernels_tma.cu — the split-precision level kernel with the A operand loaded by
-// TMA from BF16 pieces (block sizes b that are multiples of 32 and whose output
+// TMA from BF16 pieces (block sizes b that are multiples of 16 and whose output
 // blocks hold a multiple of 128 rows).
 //
 // The operands are those of level_tc_kernel (kernels_tc.cu): rows of stored
 // parent blocks gathered through G times X.  Here the parent temporaries (and A,
 // pre-split once) are stored as BF16 pieces, [node][block][piece][b^m], so every
 // 32-wide contraction stage of a 128-row tile is one box of one stored block
-// (b = 16: two boxes, one per 16-wide MMA slice, in 32-byte swizzle):
+// when b is a multiple of 32 (64-byte swizzle); otherwise (b = 16, 48, 80, ...)
+// each 16-wide MMA slice of the stage is a box of the stored block holding that
+// slice (32-byte swizzle):
 //   * insertion position q = 0: the contraction index is the block's fastest
-//     mode, rows are b apart -> a 3-D K-major box {32, 128, NP};
-//   * q >= 1: rows are contiguous in runs of b^q >= 32 and the contraction index
-//     is b^q apart -> a 5-D MN-major box {32 rows, 32 k, atoms, outer, NP} in
-//     32-row (64-byte) swizzle atoms,
+//     mode, rows are b apart -> a 3-D K-major box {32 (16), 128, NP};
+//   * q >= 1: rows are contiguous in runs of b^q and the contraction index is
+//     b^q apart -> a 5-D MN-major box {32 (16) rows, 32 (16) k, atoms, outer, NP}
+//     in 32-row (16-row) swizzle atoms; when b^q neither divides 128 nor is a
+//     multiple of it (b^q = 48, 80, ...), the 16-row atoms of the tile are
+//     loaded one by one, the pieces of an atom side by side,
 // which is how the permutation of App. A (permute before dgemm) becomes a choice
 // of tensor map and operand major-ness per stage instead of a data movement.
 //
@@ -50,6 +54,11 @@ __host__ __device__ constexpr bool d0_group_end(int ks, int nk)
     return ks == nk - 1 || ks == T_GS0 - 1 || (ks >= T_GS0 && (ks - T_GS0) % T_GS == T_GS - 1);
 }
 __host__ __device__ constexpr int d0_groups(int nk) { return nk <= T_GS0 ? 1 : 1 + (nk - T_GS0 + T_GS - 1) / T_GS; }
+
+// A run of b^q contiguous rows (insertion position q >= 1) that neither holds
+// whole 128-row tiles nor divides 128 (b^q = 48, 80, 112, 144, ...): the tile's
+// 16-row atoms are loaded one by one.
+__host__ __device__ constexpr bool atomwise_run(int bq) { return (bq % 128) != 0 && (128 % bq) != 0; }
 
 template <int NP>
 struct SmemT {
@@ -91,7 +100,7 @@ __device__ __forceinline__ void tmem_fold_n(float* acc, uint32_t taddr, int n)
 
 }  // namespace
 
-template <int NP, int OUT, bool B16>
+template <int NP, int OUT, bool SW32>
 __global__ void __launch_bounds__(T_THREADS, 1)
 level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restrict__ insts,
                  const Tile* __restrict__ tiles, int ntiles, int* status, int narrow)
@@ -157,7 +166,6 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int pr = t.row0 / I.R, rr0 = t.row0 - pr * I.R;
                 const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
                 const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
-                constexpr bool b16 = B16;
                 for (int ks = 0; ks < nk; ++ks) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                     const int k0 = ks * TC_KC;
@@ -166,22 +174,35 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     // X box rows: the tile's columns rounded up to 32
                     const int xsel = (t.ncols + 31) / 32 - 1;
                     const uint32_t x_bytes = (uint32_t)(NP * (xsel + 1) * 32 * TC_KC * 2);
-                    if (b16) {
-                        // two stored blocks per stage, one per 16-wide K slice (the
-                        // second is absent in the last stage when n-bar is odd)
-                        const int ib0 = k0 >> 4;
-                        const int nblk = ib0 + 1 < I.nbar ? 2 : 1;
-                        mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(nblk * NP * (S::A_PLANE / 2)) + x_bytes);
-                        for (int h = 0; h < nblk; ++h) {
-                            const int32_t gq = __ldg(Grow + ib0 + h);
+                    if (SW32) {
+                        // one box per 16-wide K slice, each from the stored block
+                        // holding that slice (the second slice is absent when the
+                        // contraction ends inside the stage)
+                        const int nsl = k0 + 16 < I.Ktot ? 2 : 1;
+                        mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(nsl * NP * (S::A_PLANE / 2)) + x_bytes);
+                        for (int h = 0; h < nsl; ++h) {
+                            const int k = k0 + 16 * h;
+                            const int ib = k / I.b, a0 = k - ib * I.b;
+                            const int32_t gq = __ldg(Grow + ib);
                             const int q = gq & 7;
                             const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
                             const uint32_t dA = sA + (uint32_t)(h * NP * (S::A_PLANE / 2));
                             if (q == 0) {
-                                tma_load_3d(dA, &TI.tmA[0], 0, rr0, bp, full_bar(stage));
+                                tma_load_3d(dA, &TI.tmA[0], a0, rr0, bp, full_bar(stage));
                             } else {
                                 const int bq = I.bpow[q];
-                                tma_load_5d(dA, &TI.tmA[q], 0, 0, (rr0 % bq) >> 4, rr0 / bq, bp, full_bar(stage));
+                                if (atomwise_run(bq)) {
+                                    // 16-row atoms one by one (each lies inside one run of
+                                    // b^q contiguous rows), all pieces of an atom together
+#pragma unroll 1
+                                    for (int a = 0; a < TC_BM / 16; ++a) {
+                                        const int r = rr0 + 16 * a;
+                                        tma_load_5d(dA + (uint32_t)(a * NP * 512), &TI.tmA[q], 0, a0, (r % bq) >> 4, r / bq,
+                                                    bp, full_bar(stage));
+                                    }
+                                } else {
+                                    tma_load_5d(dA, &TI.tmA[q], 0, a0, (rr0 % bq) >> 4, rr0 / bq, bp, full_bar(stage));
+                                }
                             }
                         }
                     } else {
@@ -223,7 +244,6 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int pr = t.row0 / I.R;
                 const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
                 const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
-                constexpr bool b16 = B16;
                 const int nmma = (t.ncols + 15) & ~15;
                 const uint32_t idesc_k = idesc_bf16(nmma), idesc_mn = idesc_bf16_amn(nmma);
                 // B piece planes are as tall as the X box the producer used
@@ -232,25 +252,32 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 tile_phase ^= 1u;
                 tc_fence_after();
                 for (int ks = 0; ks < nk; ++ks) {
-                    // A major-ness and presence of the two 16-wide K slices of the stage
-                    bool mnk[2], valid[2];
-                    if (b16) {
-                        const int ib0 = ks * 2;
-                        valid[0] = true;
-                        valid[1] = ib0 + 1 < I.nbar;
-                        mnk[0] = (__ldg(Grow + ib0) & 7) != 0;
-                        mnk[1] = valid[1] && (__ldg(Grow + ib0 + 1) & 7) != 0;
+                    // A major-ness, atom layout and presence of the two 16-wide K slices
+                    bool mnk[2], valid[2], atom[2];
+                    if (SW32) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int k = ks * TC_KC + 16 * h;
+                            valid[h] = k < I.Ktot;
+                            const int q = valid[h] ? (__ldg(Grow + k / I.b) & 7) : 0;
+                            mnk[h] = q != 0;
+                            atom[h] = q != 0 && atomwise_run(I.bpow[q]);
+                        }
                     } else {
                         const int ib = (ks * TC_KC) / I.b;
                         mnk[0] = mnk[1] = (__ldg(Grow + ib) & 7) != 0;
                         valid[0] = valid[1] = true;
+                        atom[0] = atom[1] = false;
                     }
                     if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
                     const uint32_t sB = sA + NP * S::A_PLANE;
                     auto adesc = [&](int s, int kh) {
-                        if (b16) {
+                        if (SW32) {
+                            if (atom[kh])
+                                return smem_desc_sw32_mn_lbo(sA + (uint32_t)(kh * NP * (S::A_PLANE / 2) + s * 512),
+                                                             (uint32_t)(NP * 512));
                             const uint32_t a = sA + (uint32_t)((kh * NP + s) * (S::A_PLANE / 2));
                             return mnk[kh] ? smem_desc_sw32_mn(a) : smem_desc_sw32(a);
                         }
@@ -515,15 +542,15 @@ static int launch_tma_variant(const TmaInst& inst0, const TmaInst* d_insts, cons
 }
 
 template <int NP, int OUT>
-static int launch_tma_b(bool b16, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
+static int launch_tma_b(bool sw32, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
                         int grid, int* d_status, int narrow, cudaStream_t s)
 {
-    return b16 ? launch_tma_variant<NP, OUT, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s)
+    return sw32 ? launch_tma_variant<NP, OUT, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s)
                : launch_tma_variant<NP, OUT, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
 }
 
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, int out_kind, bool b16, int max_cols, cudaStream_t s)
+                     int num_sms, int* d_status, int out_kind, bool sw32, int max_cols, cudaStream_t s)
 {
     const int narrow = max_cols <= 64 ? 1 : 0;
     if (ntiles <= 0) return 0;
@@ -532,15 +559,15 @@ int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, c
     const int grid = ntiles < num_sms ? ntiles : num_sms;
     if (npiece == 2) {
         switch (out_kind) {
-        case TMA_OUT_PIECES: return launch_tma_b<2, TMA_OUT_PIECES>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
-        case TMA_OUT_C: return launch_tma_b<2, TMA_OUT_C>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
-        default: return launch_tma_b<2, TMA_OUT_F32>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+        case TMA_OUT_PIECES: return launch_tma_b<2, TMA_OUT_PIECES>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+        case TMA_OUT_C: return launch_tma_b<2, TMA_OUT_C>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+        default: return launch_tma_b<2, TMA_OUT_F32>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
         }
     }
     switch (out_kind) {
-    case TMA_OUT_PIECES: return launch_tma_b<3, TMA_OUT_PIECES>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
-    case TMA_OUT_C: return launch_tma_b<3, TMA_OUT_C>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
-    default: return launch_tma_b<3, TMA_OUT_F32>(b16, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+    case TMA_OUT_PIECES: return launch_tma_b<3, TMA_OUT_PIECES>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+    case TMA_OUT_C: return launch_tma_b<3, TMA_OUT_C>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+    default: return launch_tma_b<3, TMA_OUT_F32>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
     }
 }
 

@@ -66,8 +66,9 @@ struct TmaInst {
 // out_kind: TMA_OUT_PIECES writes the next level's operand as BF16 pieces,
 // TMA_OUT_C writes FP32 C (the last level, k = 0: a row's columns contiguous),
 // TMA_OUT_F32 writes FP32 at a level k >= 1 (the all-but-one result).
-// b16: every instance of the launch has b = 16 (two 16-wide blocks per stage);
-// otherwise every instance has b a multiple of 32.
+// sw32: every instance of the launch has b an odd multiple of 16 (one box per
+// 16-wide K slice, 32-byte swizzle); otherwise every instance has b a multiple
+// of 32 (one box per 32-wide stage).
 constexpr int TMA_OUT_PIECES = 0, TMA_OUT_C = 1, TMA_OUT_F32 = 2;
 
 // A wait that never completes, bounded by limit_ns; raises *d_status on timeout.
@@ -75,7 +76,7 @@ int launch_wait_probe(int* d_status, unsigned long long limit_ns, cudaStream_t s
 // max_cols: the widest tile of the launch; launches of tiles <= 64 columns wide
 // run with more, smaller pipeline stages.
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
-                     int num_sms, int* d_status, int out_kind, bool b16, int max_cols, cudaStream_t s);
+                     int num_sms, int* d_status, int out_kind, bool sw32, int max_cols, cudaStream_t s);
 int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, int npiece, cudaStream_t s);
 
 // Tensor maps of a BF16-piece parent array with nblocks stored blocks (all

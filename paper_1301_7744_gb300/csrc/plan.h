@@ -34,10 +34,16 @@ int make_shape(int m, int64_t n, int64_t p, int b, Shape* s);
 // use the small-tile kernel (128 x 64 tiles).
 inline bool tc_small_mode(const Shape& s) { return s.nbar * s.b <= 64; }
 
-// Split-precision shapes whose block size is a multiple of 32 and whose
+// Split-precision shapes whose block size is a multiple of 16 and whose
 // output blocks hold a multiple of 128 rows take the TMA-fed kernel
 // (temporaries stored as BF16 pieces).
-inline bool tc_tma_mode(const Shape& s) { return !tc_small_mode(s) && (s.b % 32 == 0 || s.b == 16) && s.R % 128 == 0; }
+inline bool tc_tma_mode(const Shape& s) { return !tc_small_mode(s) && s.b % 16 == 0 && s.R % 128 == 0; }
+// TMA-fed block sizes other than 32, 64 and multiples of 128 load one box per
+// 16-wide K slice (32-byte swizzle, 16-row atoms) instead of one per 32-wide
+// stage (64-byte swizzle, 32-row atoms): every b^q is then a multiple of the
+// atom height.
+inline bool tma_sw32_b(int b) { return !(b == 32 || b == 64 || b % 128 == 0); }
+inline bool tma_sw32(const Shape& s) { return tma_sw32_b(s.b); }
 
 // Host tile list and G table of level d (appended to the given vectors).
 // Tiles cover, for every parent node, P_out * R rows in steps of BM and the

@@ -237,7 +237,7 @@ int launch_step(sttsm_serve_s* H)
     int64_t split_blocks = 0;
     std::vector<const Req*> asplit;            // TMA requests whose A is split this step
     // groups: 0 gathered A, 1 small tiles, 2 / 3 TMA writing pieces / C with b a
-    // multiple of 32, 4 / 5 the same with b = 16
+    // multiple of 32, 4 / 5 the same with b an odd multiple of 16
     constexpr int NG = 6;
     std::vector<TcInst> insts[2];
     std::vector<TmaInst> tinsts[NG - 2];
@@ -257,7 +257,7 @@ int launch_step(sttsm_serve_s* H)
             R.split_done = true;
         }
         const bool last = R.level == R.s.m - 1;
-        const int g = R.tma ? (last ? 3 : 2) + (R.s.b == 16 ? 2 : 0) : (R.small ? 1 : 0);
+        const int g = R.tma ? (last ? 3 : 2) + (tma_sw32(R.s) ? 2 : 0) : (R.small ? 1 : 0);
         int32_t e;
         if (g < 2) { e = (int32_t)insts[g].size(); insts[g].push_back(R.inst[R.level]); }
         else { e = (int32_t)tinsts[g - 2].size(); tinsts[g - 2].push_back(R.tinst[R.level]); }

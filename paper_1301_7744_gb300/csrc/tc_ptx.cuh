@@ -125,6 +125,20 @@ __device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, float* v)
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 16 consecutive FP32 columns in one load and one wait.
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Shared-memory matrix descriptor (tcgen05): start address, leading and
 // stride byte offsets (16-byte units), fixed version bits 46-48 = 0b001,
 // swizzle mode in bits 61-63 (4 = 64-byte swizzle).
@@ -196,6 +210,20 @@ __device__ __forceinline__ uint64_t smem_desc_sw32_mn(uint32_t addr)
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
     d |= (uint64_t)(512 >> 4) << 16;
+    d |= (uint64_t)(256 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
+    return d;
+}
+
+// MN-major SW32 operand whose 16-element M atoms are lbo bytes apart (the
+// atoms of several pieces interleaved, piece planes 512 B apart inside an atom
+// group); 8-row K groups 256 B apart.
+__device__ __forceinline__ uint64_t smem_desc_sw32_mn_lbo(uint32_t addr, uint32_t lbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)(256 >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)6 << 61;

@@ -12,7 +12,11 @@ from helpers import device_bcss_from_dense, inputs, rel_fro, xcol
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "bf16x6": 1e-6, "bf16x3": 1e-6}
+# BF16X3 keeps 16 significand bits of each operand in two BF16 pieces and drops
+# the lo x lo product: about 3 x 2^-16 = 4.6e-5 relative per product at worst.
+# This entry point and sttsm_bcss run different kernels for it (gather-fed and
+# TMA-fed), which may differ by that much; 1e-4 bounds it.
+TOL = {"fp64": 1e-12, "bf16x6": 1e-6, "bf16x3": 1e-4}
 
 
 @pytest.fixture(scope="module")
