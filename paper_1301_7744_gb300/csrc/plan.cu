@@ -112,6 +112,27 @@ void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std:
     }
 }
 
+int64_t level_tile_count(const Shape& s, int d, int BM, int BN)
+{
+    const LevelShape& L = s.lv[d];
+    const int64_t row_tiles = (L.P_out * s.R + BM - 1) / BM;
+    int32_t u[STTSM_MAX_M];
+    int64_t count = 0;
+    for (int64_t par = 0; par < L.nodes_parent; ++par) {
+        int64_t children = s.pbar;
+        if (d > 0) {
+            colex_unrank(par, d, u);
+            children = (int64_t)u[0] + 1;
+        }
+        const int64_t ncols = children * s.b;
+        int64_t w = BN;
+        const int64_t nct = (ncols + BN - 1) / BN;
+        if (BN >= 128 && nct > 1) w = ((ncols + nct - 1) / nct + 15) / 16 * 16;
+        count += row_tiles * ((ncols + w - 1) / w);
+    }
+    return count;
+}
+
 namespace {
 std::mutex g_mu;
 std::map<std::tuple<int, int, int64_t, int64_t, int, int, int>, DevPlan*> g_plans;

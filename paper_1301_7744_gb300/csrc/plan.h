@@ -49,6 +49,8 @@ inline bool tma_sw32(const Shape& s) { return tma_sw32_b(s.b); }
 // Tiles cover, for every parent node, P_out * R rows in steps of BM and the
 // parent's children * b columns in steps of BN.
 void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles);
+// Number of tiles build_level_tiles emits for level d (counted, not built).
+int64_t level_tile_count(const Shape& s, int d, int BM, int BN);
 // G table of level d ([P_out][nbar]) followed by its offset table OFF
 // ([k+1][R]); level_G_size is the length of the G part.
 void build_level_G(const Shape& s, int d, std::vector<int32_t>& G);

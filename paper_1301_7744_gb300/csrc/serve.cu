@@ -11,6 +11,16 @@
 // completes the request is done, its latency (submit -> completion seen by the
 // scheduler) is recorded and its workspace returns to the arena.  Up to two
 // steps are in flight, so the host builds step s+1 while the GPU runs step s.
+//
+// Nothing in the scheduler loop allocates device or pinned memory or waits for
+// the whole stream: the level tables (G) live in a table region reserved at
+// create time (first-fit, entries of shapes no active request uses are evicted
+// when it is full), the per-step staging buffers (pinned host + device) have a
+// fixed size (a step takes active requests in turn until its staging is full;
+// the others advance at the next step), and the step events come from a fixed
+// pool.  Admission takes queued requests in arrival order but lets a later
+// request pass one whose workspace does not fit yet, until the waiting one is
+// older than SERVE_AGE_CAP_S: from then on nothing passes it.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -35,6 +45,14 @@ int peek_status_word();     // capi.cu
 namespace {
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr size_t SERVE_TABLE_BYTES = (size_t)64 << 20;     // level tables (G), outside the budget
+constexpr size_t SERVE_STAGING_BYTES = (size_t)32 << 20;   // per staging buffer (two), outside the budget
+constexpr double SERVE_AGE_CAP_S = 0.020;                  // later requests stop passing one older than this
+constexpr int SERVE_EVENTS = 4;                            // step events (at most two steps in flight)
+constexpr int SERVE_PASS_WINDOW = 64;                      // queued requests looked at per admission round
+constexpr size_t SERVE_UPLOAD_BYTES = (size_t)4 << 20;     // pinned buffer for level-table uploads
+constexpr size_t SERVE_STAGING_SLACK = 4096;               // alignment of a step's staging segments
 
 double now_s()
 {
@@ -103,10 +121,20 @@ struct Req {
     std::vector<Tile> tiles[STTSM_MAX_M];
     std::vector<TcInst> inst;       // per level (released when the request is done)
     std::vector<TmaInst> tinst;     // per level, TMA-fed requests only
+    bool tables_held = false;       // holds a reference on its shape's level tables
+};
+
+// Level tables of one shape (m, nbar, b): the G table and offset table of
+// every level, one allocation in the table region.
+struct TableSet {
+    size_t off = 0, bytes = 0;
+    size_t level_off[STTSM_MAX_M] = {};
+    int refs = 0;
+    uint64_t last_use = 0;
 };
 
 struct StepRec {
-    cudaEvent_t ev;
+    int ev;                          // index into the handle's event pool
     std::vector<uint64_t> finishing;
 };
 
@@ -134,35 +162,89 @@ struct sttsm_serve_s {
     std::vector<uint64_t> active;
     uint64_t next_ticket = 1;
     uint64_t n_submitted = 0, n_admitted = 0, n_completed = 0;
-    std::map<std::tuple<int, int64_t, int, int>, std::pair<int32_t*, std::vector<int32_t>>> G;
+    char* table_base = nullptr;
+    Arena* tables = nullptr;
+    char* upload_h = nullptr;            // pinned
+    cudaEvent_t upload_done = nullptr;
+    std::map<std::tuple<int, int64_t, int>, TableSet> G;   // (m, nbar, b) -> tables
+    uint64_t use_clock = 0;
     Staging stg[2];
     int cur = 0;
+    cudaEvent_t events[SERVE_EVENTS] = {};
+    int next_event = 0;
     std::deque<StepRec> inflight;
     int error = 0;
 };
 
 namespace {
 
-int ensure_G(sttsm_serve_s* H, const Shape& s, int d, const int32_t** out)
+// The level tables of shape s, built and copied into the table region on first
+// use; returns nullptr when the region has no room even after evicting every
+// table set no active request holds (the request then waits).
+TableSet* acquire_tables(sttsm_serve_s* H, const Shape& s, int* rc)
 {
-    auto key = std::make_tuple(s.m, s.nbar, s.b, d);
+    *rc = STTSM_OK;
+    auto key = std::make_tuple(s.m, s.nbar, s.b);
     auto it = H->G.find(key);
     if (it == H->G.end()) {
-        std::vector<int32_t> g;
-        build_level_G(s, d, g);
-        int32_t* dg = nullptr;
-        if (cudaMalloc(&dg, g.size() * sizeof(int32_t)) != cudaSuccess) return STTSM_ERR_NOMEM;
-        it = H->G.emplace(key, std::make_pair(dg, std::move(g))).first;
-        if (cudaMemcpyAsync(dg, it->second.second.data(), it->second.second.size() * sizeof(int32_t),
-                            cudaMemcpyHostToDevice, H->stream) != cudaSuccess)
-            return STTSM_ERR_CUDA;
+        std::vector<int32_t> g[STTSM_MAX_M];
+        TableSet T;
+        size_t bytes = 0;
+        for (int d = 0; d < s.m; ++d) {
+            build_level_G(s, d, g[d]);
+            T.level_off[d] = bytes;
+            bytes = up256(bytes + g[d].size() * sizeof(int32_t));
+        }
+        T.bytes = bytes;
+        while (!H->tables->alloc(bytes, &T.off)) {
+            // evict the least recently used table set that no request holds
+            auto victim = H->G.end();
+            for (auto v = H->G.begin(); v != H->G.end(); ++v)
+                if (v->second.refs == 0 && (victim == H->G.end() || v->second.last_use < victim->second.last_use))
+                    victim = v;
+            if (victim == H->G.end()) return nullptr;
+            H->tables->release(victim->second.off, victim->second.bytes);
+            H->G.erase(victim);
+        }
+        // upload through the pinned upload buffer (chunks of its size; it is reused
+        // once the previous chunk's copy has finished)
+        for (int d = 0; d < s.m; ++d) {
+            const char* src = (const char*)g[d].data();
+            const size_t total = g[d].size() * sizeof(int32_t);
+            for (size_t done = 0; done < total;) {
+                const size_t n = std::min(total - done, SERVE_UPLOAD_BYTES);
+                if (cudaEventSynchronize(H->upload_done) != cudaSuccess) { *rc = STTSM_ERR_CUDA; return nullptr; }
+                memcpy(H->upload_h, src + done, n);
+                if (cudaMemcpyAsync(H->table_base + T.off + T.level_off[d] + done, H->upload_h, n, cudaMemcpyHostToDevice,
+                                    H->stream) != cudaSuccess ||
+                    cudaEventRecord(H->upload_done, H->stream) != cudaSuccess) {
+                    *rc = STTSM_ERR_CUDA;
+                    return nullptr;
+                }
+                done += n;
+            }
+        }
+        it = H->G.emplace(key, T).first;
     }
-    *out = it->second.first;
-    return STTSM_OK;
+    it->second.refs += 1;
+    it->second.last_use = ++H->use_clock;
+    return &it->second;
+}
+
+void release_tables(sttsm_serve_s* H, const Shape& s)
+{
+    auto it = H->G.find(std::make_tuple(s.m, s.nbar, s.b));
+    if (it != H->G.end() && it->second.refs > 0) it->second.refs -= 1;
+}
+
+// Staging bytes one request needs at its current level: its descriptor and tiles.
+size_t staging_need(const Req& R)
+{
+    return (R.tma ? sizeof(TmaInst) : sizeof(TcInst)) + R.tiles[R.level].size() * sizeof(Tile) + sizeof(SplitDesc) + 768;
 }
 
 // Builds the request's per-level tiles and descriptors once it has a workspace.
-int admit(sttsm_serve_s* H, Req& R)
+int admit(sttsm_serve_s* H, Req& R, const TableSet& T)
 {
     const Shape& s = R.s;
     char* base = H->arena_base + R.ws_off;
@@ -179,9 +261,7 @@ int admit(sttsm_serve_s* H, Req& R)
     if (R.tma) R.tinst.assign(s.m, TmaInst());
     for (int d = 0; d < s.m; ++d) {
         build_level_tiles(s, d, TC_BM, box, 0, R.tiles[d]);
-        const int32_t* G = nullptr;
-        const int rc = ensure_G(H, s, d, &G);
-        if (rc != STTSM_OK) return rc;
+        const int32_t* G = (const int32_t*)(H->table_base + T.off + T.level_off[d]);
         const LevelShape& LS = s.lv[d];
         TcInst& T = R.inst[d];
         memset(&T, 0, sizeof(T));
@@ -215,20 +295,6 @@ int admit(sttsm_serve_s* H, Req& R)
     return STTSM_OK;
 }
 
-int grow_staging(sttsm_serve_s* H, Staging& S, size_t need)
-{
-    if (S.cap >= need) return STTSM_OK;
-    if (cudaStreamSynchronize(H->stream) != cudaSuccess) return STTSM_ERR_CUDA;
-    if (S.h) cudaFreeHost(S.h);
-    if (S.d) cudaFree(S.d);
-    S.h = nullptr; S.d = nullptr; S.cap = 0;
-    const size_t cap = std::max(need + need / 2, (size_t)1 << 20);
-    if (cudaHostAlloc((void**)&S.h, cap, cudaHostAllocDefault) != cudaSuccess) return STTSM_ERR_NOMEM;
-    if (cudaMalloc((void**)&S.d, cap) != cudaSuccess) return STTSM_ERR_NOMEM;
-    S.cap = cap;
-    return STTSM_OK;
-}
-
 // One step: the X split of newly admitted requests, then per tile kind one
 // level launch over every active request at its current level.
 int launch_step(sttsm_serve_s* H)
@@ -242,9 +308,14 @@ int launch_step(sttsm_serve_s* H)
     std::vector<TcInst> insts[2];
     std::vector<TmaInst> tinsts[NG - 2];
     std::vector<Tile> tiles[NG];
-    std::vector<uint64_t> finishing;
+    std::vector<uint64_t> finishing, stepped, waiting;
+    size_t need = 0;
     for (uint64_t tk : H->active) {
         Req& R = H->reqs[tk];
+        const size_t rn = staging_need(R);
+        if (need + rn > SERVE_STAGING_BYTES - SERVE_STAGING_SLACK) { waiting.push_back(tk); continue; }   // next step
+        need += rn;
+        stepped.push_back(tk);
         if (!R.split_done) {
             SplitDesc sd;
             sd.X = (const float*)R.d.X;
@@ -274,10 +345,9 @@ int launch_step(sttsm_serve_s* H)
     o_s = off;
     off = up256(off + split.size() * sizeof(SplitDesc));
     Staging& S = H->stg[H->cur];
-    if (S.copied && cudaEventSynchronize(S.copied) != cudaSuccess) return STTSM_ERR_CUDA;
-    int rc = grow_staging(H, S, off);
-    if (rc != STTSM_OK) return rc;
-    if (!S.copied && cudaEventCreateWithFlags(&S.copied, cudaEventDisableTiming) != cudaSuccess) return STTSM_ERR_CUDA;
+    if (off > S.cap) return STTSM_ERR_NOMEM;   // cannot happen: requests were taken while they fit
+    // the copy that last read this staging buffer (two steps back) has finished
+    if (cudaEventSynchronize(S.copied) != cudaSuccess) return STTSM_ERR_CUDA;
     for (int k = 0; k < NG - 2; ++k)
         if (!tinsts[k].empty()) memcpy(S.h + o_ti[k], tinsts[k].data(), tinsts[k].size() * sizeof(TmaInst));
     for (int k = 0; k < 2; ++k)
@@ -314,9 +384,10 @@ int launch_step(sttsm_serve_s* H)
         if (lrc != 0) return STTSM_ERR_CUDA;
     }
     H->cur ^= 1;
-    // advance every request by one level; the finished ones wait for this step's event
-    std::vector<uint64_t> still;
-    for (uint64_t tk : H->active) {
+    // advance the stepped requests by one level (the finished ones wait for this
+    // step's event); requests left out of this step go first in the next
+    std::vector<uint64_t> still = waiting;
+    for (uint64_t tk : stepped) {
         Req& R = H->reqs[tk];
         if (++R.level == R.s.m) {
             R.state = Q_FINISHING;
@@ -327,8 +398,9 @@ int launch_step(sttsm_serve_s* H)
     }
     H->active.swap(still);
     StepRec rec;
-    if (cudaEventCreateWithFlags(&rec.ev, cudaEventDisableTiming) != cudaSuccess) return STTSM_ERR_CUDA;
-    if (cudaEventRecord(rec.ev, H->stream) != cudaSuccess) return STTSM_ERR_CUDA;
+    rec.ev = H->next_event;
+    H->next_event = (H->next_event + 1) % SERVE_EVENTS;
+    if (cudaEventRecord(H->events[rec.ev], H->stream) != cudaSuccess) return STTSM_ERR_CUDA;
     rec.finishing.swap(finishing);
     H->inflight.push_back(std::move(rec));
     return STTSM_OK;
@@ -341,7 +413,7 @@ void scheduler(sttsm_serve_s* H)
         bool progress = false;
         // retire completed steps
         while (!H->inflight.empty()) {
-            const cudaError_t q = cudaEventQuery(H->inflight.front().ev);
+            const cudaError_t q = cudaEventQuery(H->events[H->inflight.front().ev]);
             if (q == cudaErrorNotReady) break;
             const double t = now_s();
             std::lock_guard<std::mutex> lock(H->mu);
@@ -351,28 +423,46 @@ void scheduler(sttsm_serve_s* H)
                 R.state = Q_DONE;
                 R.t_done = t;
                 H->arena->release(R.ws_off, R.ws_bytes);
+                if (R.tables_held) { release_tables(H, R.s); R.tables_held = false; }
                 for (int d = 0; d < STTSM_MAX_M; ++d) std::vector<Tile>().swap(R.tiles[d]);
                 std::vector<TcInst>().swap(R.inst);
                 std::vector<TmaInst>().swap(R.tinst);
                 ++H->n_completed;
             }
-            cudaEventDestroy(H->inflight.front().ev);
             H->inflight.pop_front();
             progress = true;
         }
-        // admission in arrival order while the workspace fits
+        // admission in arrival order; a request whose workspace (or level tables)
+        // does not fit yet is passed by later ones until it is older than the age
+        // cap, after which nothing passes it
         {
             std::lock_guard<std::mutex> lock(H->mu);
-            while (!H->queue.empty() && !H->error) {
-                Req& R = H->reqs[H->queue.front()];
+            const double t = now_s();
+            int scanned = 0;
+            for (auto qi = H->queue.begin(); qi != H->queue.end() && !H->error && scanned < SERVE_PASS_WINDOW;
+                 ++scanned) {
+                Req& R = H->reqs[*qi];
                 size_t off = 0;
-                if (!H->arena->alloc(R.ws_bytes, &off)) break;
+                bool ok = H->arena->alloc(R.ws_bytes, &off);
+                TableSet* T = nullptr;
+                if (ok) {
+                    int rc = STTSM_OK;
+                    T = acquire_tables(H, R.s, &rc);
+                    if (rc != STTSM_OK) { H->error = rc; break; }
+                    if (!T) { H->arena->release(off, R.ws_bytes); ok = false; }
+                }
+                if (!ok) {
+                    if (t - R.t_submit > SERVE_AGE_CAP_S) break;   // it waits; nothing passes it
+                    ++qi;
+                    continue;
+                }
                 R.ws_off = off;
-                const int rc = admit(H, R);
+                R.tables_held = true;
+                const int rc = admit(H, R, *T);
                 if (rc != STTSM_OK) { H->error = rc; break; }
                 R.state = Q_ACTIVE;
-                H->active.push_back(H->queue.front());
-                H->queue.pop_front();
+                H->active.push_back(*qi);
+                qi = H->queue.erase(qi);
                 ++H->n_admitted;
                 progress = true;
             }
@@ -393,8 +483,12 @@ void destroy(sttsm_serve_s* H)
     H->stop.store(true);
     if (H->th.joinable()) H->th.join();
     if (H->stream) cudaStreamSynchronize(H->stream);
-    for (auto& r : H->inflight) cudaEventDestroy(r.ev);
-    for (auto& kv : H->G) cudaFree(kv.second.first);
+    for (cudaEvent_t& e : H->events)
+        if (e) cudaEventDestroy(e);
+    if (H->table_base) cudaFree(H->table_base);
+    delete H->tables;
+    if (H->upload_h) cudaFreeHost(H->upload_h);
+    if (H->upload_done) cudaEventDestroy(H->upload_done);
     for (Staging& S : H->stg) {
         if (S.h) cudaFreeHost(S.h);
         if (S.d) cudaFree(S.d);
@@ -421,12 +515,28 @@ int sttsm_serve_create(size_t hbm_budget_bytes, int prec, int queue_cap, void** 
     cudaGetDevice(&H->device);
     if (cudaDeviceGetAttribute(&H->sms, cudaDevAttrMultiProcessorCount, H->device) != cudaSuccess || H->sms <= 0) H->sms = 148;
     H->status = batch_status_word();
-    if (!H->status || cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMalloc((void**)&H->arena_base, up256(hbm_budget_bytes)) != cudaSuccess) {
+    bool ok = H->status && cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc((void**)&H->arena_base, up256(hbm_budget_bytes)) == cudaSuccess &&
+              cudaMalloc((void**)&H->table_base, SERVE_TABLE_BYTES) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k) {
+        Staging& S = H->stg[k];
+        ok = cudaHostAlloc((void**)&S.h, SERVE_STAGING_BYTES, cudaHostAllocDefault) == cudaSuccess &&
+             cudaMalloc((void**)&S.d, SERVE_STAGING_BYTES) == cudaSuccess &&
+             cudaEventCreateWithFlags(&S.copied, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventRecord(S.copied, H->stream) == cudaSuccess;
+        if (ok) S.cap = SERVE_STAGING_BYTES;
+    }
+    for (int k = 0; k < SERVE_EVENTS && ok; ++k)
+        ok = cudaEventCreateWithFlags(&H->events[k], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void**)&H->upload_h, SERVE_UPLOAD_BYTES, cudaHostAllocDefault) == cudaSuccess &&
+         cudaEventCreateWithFlags(&H->upload_done, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventRecord(H->upload_done, H->stream) == cudaSuccess;
+    if (!ok) {
         destroy(H);
         return STTSM_ERR_NOMEM;
     }
     H->arena = new Arena(up256(hbm_budget_bytes));
+    H->tables = new Arena(SERVE_TABLE_BYTES);
     H->th = std::thread(scheduler, H);
     *handle = H;
     return STTSM_OK;
@@ -456,6 +566,11 @@ int sttsm_serve_submit(void* h, const sttsm_desc* d, uint64_t* ticket)
     R.buf_off[1] = off;
     off += up256((size_t)R.s.buf_elems[1] * esz);
     R.ws_bytes = std::max<size_t>(off, 256);
+    // a request must fit one step's staging buffer at every level
+    for (int lv = 0; lv < R.s.m; ++lv)
+        if (level_tile_count(R.s, lv, TC_BM, R.small ? TC_SMALL_BN : TC_BN) * sizeof(Tile) + sizeof(TmaInst) + 1024 >
+            SERVE_STAGING_BYTES - SERVE_STAGING_SLACK)
+            return STTSM_ERR_NOMEM;
     std::lock_guard<std::mutex> lock(H->mu);
     if (H->error) return H->error;
     if (R.ws_bytes > H->arena->size()) return STTSM_ERR_NOMEM;

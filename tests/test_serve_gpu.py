@@ -141,3 +141,67 @@ def test_both_tma_forms_and_small_tiles_in_one_step(st):
         got = r["C"].double().cpu().numpy()
         assert np.array_equal(got, alone(st, r)), (r["m"], r["n"], r["b"])
         assert rel_fro(got, oracle_C_bcss(r["A"], r["X"], r["m"], r["p"], r["b"])) <= 1e-6
+
+
+def test_later_small_requests_pass_one_that_does_not_fit_yet(st):
+    """Budget for one big request plus a margin: while the first big request runs,
+    a second big one cannot be admitted; small requests submitted after it are
+    admitted in the margin and finish before it (admission lets them pass a
+    request whose workspace does not fit yet, within the age cap)."""
+    big = [make_request(st, 9500 + i, 3, 384, 384, 16) for i in range(2)]
+    small = [make_request(st, 9600 + i, 5, 16, 16, 4) for i in range(6)]
+    torch.cuda.synchronize()
+    need_big = st.sttsm_workspace_size(3, 384, 384, 16, st.STTSM_BF16X6)
+    need_small = st.sttsm_workspace_size(5, 16, 16, 4, st.STTSM_BF16X6)
+    srv = st.Server(need_big + 8 * need_small + (1 << 20))
+    order = []
+    tickets = [srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"]) for r in big]
+    tickets += [srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"]) for r in small]
+    t0 = time.time()
+    while len(order) < len(tickets):
+        for t in tickets:
+            if t not in order and srv.poll(t)[0]:
+                order.append(t)
+        assert time.time() - t0 < 60.0
+    srv.destroy()
+    second_big = tickets[1]
+    assert any(order.index(t) < order.index(second_big) for t in tickets[2:])
+    for r in big + small:
+        assert np.array_equal(r["C"].double().cpu().numpy(), alone(st, r))
+
+
+def test_full_size_classes_sampled_against_oracle(st):
+    """One request at the top of each serving class (m=3 n up to 512, m=4 up to
+    160, m=5 up to 64, m=6 up to 32), served together; 32 sampled C entries of each
+    against the FP64 oracle's entry contraction, and each result equal to the
+    request run alone."""
+    import oracle
+    from helpers import bcss_pos, rel_max
+    shapes = [(3, 512, 448, 16), (4, 128, 160, 16), (5, 48, 64, 4), (6, 24, 32, 4)]
+    reqs = []
+    for i, (m, n, p, b) in enumerate(shapes):
+        d = torch.empty(n ** m, dtype=torch.float32, device="cuda")
+        synth.dev_sym_uniform_dense(d.data_ptr(), m, n, 9700 + i, "f32", torch.cuda.current_stream().cuda_stream)
+        Ab = torch.empty(st.bcss_num_elems(m, n, b), dtype=torch.float32, device="cuda")
+        st.bcss_pack(d, Ab, m, n, b)
+        del d
+        X = synth.x_gaussian(9800 + i, p, n).astype(np.float32).astype(np.float64)
+        dX = torch.from_numpy(xcol(X)).to(device="cuda", dtype=torch.float32)
+        C = torch.full((st.bcss_num_elems(m, p, b),), float("nan"), dtype=torch.float32, device="cuda")
+        reqs.append(dict(Ab=Ab, dX=dX, C=C, X=X, m=m, n=n, p=p, b=b, seed=9700 + i))
+    torch.cuda.synchronize()
+    srv = st.Server(8 << 30)
+    tickets = [srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"]) for r in reqs]
+    wait_all(srv, tickets)
+    srv.destroy()
+    rng = np.random.default_rng(5)
+    for r in reqs:
+        m, n, p, b = r["m"], r["n"], r["p"], r["b"]
+        got = r["C"].double().cpu().numpy()
+        assert np.array_equal(got, alone(st, r))
+        J = np.sort(rng.integers(0, p, size=(32, m)), axis=1)
+        A = synth.sym_uniform_dense(m, n, r["seed"])
+        ref = oracle.sttsm_entries(A, r["X"], m, J)
+        del A
+        vals = np.array([got[bcss_pos(j, m, b)] for j in J])
+        assert rel_fro(vals, ref) <= 1e-6 and rel_max(vals, ref) <= 1e-6, (m, n, p, b)
