@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--fused-tail", type=int, default=1, choices=[0, 1, 2],
+                    help="short contractions' last two levels: 0 two launches, 1 fused in single calls "
+                         "(library default), 2 fused in batch plans and serving too")
     ap.add_argument("--no-configs", action="store_true",
                     help="leave the m4 / batch / serve short forms out of the default line")
     ap.add_argument("--configs-serve-seconds", type=float, default=10.0,
@@ -507,6 +510,7 @@ def run_m4(args, emit=True, short=False):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1301_7744_gb300 as st
+    st.sttsm_set_fused_tail(args.fused_tail)
     import synth
     import oracle
     m, n, p = 4, 128, 64
@@ -573,6 +577,7 @@ def run_abo(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1301_7744_gb300 as st
+    st.sttsm_set_fused_tail(args.fused_tail)
     import synth
     import oracle
     b = 64 if args.b == "auto" else int(args.b)
@@ -626,6 +631,7 @@ def run_batch(args, emit=True, short=False):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1301_7744_gb300 as st
+    st.sttsm_set_fused_tail(args.fused_tail)
     import synth
     prec = st.STTSM_BF16X6
     shapes = synth.batch_shapes(3, args.batch_count)
@@ -660,7 +666,7 @@ def run_batch(args, emit=True, short=False):
     torch.cuda.synchronize()
     capture_s = time.perf_counter() - t0
     steps = max(3, min(args.steps, 20))
-    tot_tc = None
+    tot_tc = tot_unfused = None
     if not args.no_extras and not short:
         # the tcgen05 small-tile kernel for the same plan (for comparison)
         st.sttsm_set_small_kernel(st.SMALL_TCGEN05)
@@ -668,6 +674,12 @@ def run_batch(args, emit=True, short=False):
         tot_tc, _ = time_steps(torch, lambda: plan_tc.run(ws), 3, 2)
         plan_tc.destroy()
         st.sttsm_set_small_kernel(st.SMALL_F32)
+        # the last two levels fused in the batch (for comparison)
+        st.sttsm_set_fused_tail(st.FUSED_TAIL_ALL)
+        plan_uf = st.BatchPlan(insts, prec, ws_budget=int(args.ws_gb * 2 ** 30))
+        tot_unfused, _ = time_steps(torch, lambda: plan_uf.run(ws), 3, 2)
+        plan_uf.destroy()
+        st.sttsm_set_fused_tail(args.fused_tail)
     clocks = ClockSampler()
     clocks.start()
     total_ms, per = time_steps(torch, lambda: plan.run(ws), steps, max(3, args.warmup))
@@ -753,6 +765,8 @@ def run_batch(args, emit=True, short=False):
                     "counts": "FP32 parents read + outputs written, every level of every instance"},
             "tcgen05_small_tile_kernel": {"value": F / (tot_tc / 3 * 1e-3) / 1e12, "unit": "TFLOP/s",
                                           "ms_per_step": tot_tc / 3} if tot_tc else None,
+            "last_two_levels_fused": {"value": F / (tot_unfused / 3 * 1e-3) / 1e12, "unit": "TFLOP/s",
+                                      "ms_per_step": tot_unfused / 3} if tot_unfused else None,
             "rel_err": {"instances_checked": len(errs), "max": max(errs), "median": float(np.median(errs)),
                         "max_elementwise": max(errs_el), "tolerance": 1e-6},
             "clocks": clk}
@@ -776,6 +790,7 @@ def run_serve(args, emit=True, seconds=None):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1301_7744_gb300 as st
+    st.sttsm_set_fused_tail(args.fused_tail)
     import synth
     prec = st.STTSM_BF16X6
     seconds = float(seconds or args.serve_seconds)
@@ -930,6 +945,7 @@ def main():
         if rank != 0:
             __graft_entry__.build()
     import paper_1301_7744_gb300 as st
+    st.sttsm_set_fused_tail(args.fused_tail)
 
     prec = st.STTSM_BF16X6 if args.prec == "bf16x6" else st.STTSM_BF16X3
     import synth

@@ -303,6 +303,19 @@ int sttsm_noalloc_selftest_wait_timeout(double limit_ms);
  * kernel.  Process-wide; affects later calls and later batch-plan runs. */
 int sttsm_set_small_kernel(int kind);
 
+/* Last two levels of short contractions (the FP32 kernel, n̄ b <= 64 and
+ * p̄ b <= 64): one launch that keeps the partially symmetric temporary T^(1)
+ * in shared memory (Fig. 5, levels m-2 and m-1: for fixed trailing indices
+ * they are the m = 2 product X_{jb0} S X_{jb1}^T of Sec. 3.2 on a slice S of
+ * T^(2)), or two launches through T^(1) in the workspace.  Both give the same
+ * bits.  mode 0 = two launches everywhere; 1 (default) = one launch in
+ * sttsm_bcss (one launch fewer per call), two in batch plans and serving
+ * (measured faster there: with many instances per launch the one-level
+ * kernel's larger tiles keep the SMs busier than the fused kernel's units);
+ * 2 = one launch everywhere.  Process-wide; affects later calls, requests
+ * submitted later and batch plans created later.  STTSM_ERR_ARG otherwise. */
+int sttsm_set_fused_tail(int mode);
+
 /* Device status word: 0 = fine; otherwise the code of the last device-side
  * failure (1 = bounded wait timed out).  Reading clears it. */
 int sttsm_device_status(void);
@@ -329,12 +342,23 @@ int sttsm_selftest_wait_timeout(double limit_ms);
 int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_t* tiles, int64_t tiles_cap,
                      int32_t* G, int64_t G_cap, int64_t* ntiles_out, int64_t* nG_out, int64_t* info);
 
+/* The units of the fused launch of levels m-2 and m-1 (sttsm_set_fused_tail)
+ * for a short-contraction shape: ntiles x 8 int32 (0, parent node J of level
+ * m-2, 0, first trailing local index tuple s0, children of J, tuples in the
+ * unit, colex-rank term of J among the C nodes, 0); *group_out = tuples per
+ * unit.  Host buffers; NULL tiles queries the count.  STTSM_ERR_UNSUPPORTED if
+ * the shape does not take the fused launch, STTSM_ERR_NOMEM if tiles_cap is
+ * too small. */
+int sttsm_plan_pair(int m, int64_t n, int64_t p, int b, int32_t* tiles, int64_t tiles_cap, int64_t* ntiles_out,
+                    int32_t* group_out);
+
 /* Per-launch timing of the library's kernels (diagnostics).  While enabled,
  * every kernel sttsm_bcss launches is bracketed by CUDA events on its
  * stream.  sttsm_profile_enable(1) clears earlier records; (0) stops.
  * sttsm_profile_read waits for the recorded events and copies up to `max`
  * records: kind (0 = FP64 level, 1 = tensor-core level with gathered A,
- * 2 = operand split, 3 = tensor-core level with TMA-fed A),
+ * 2 = operand split, 3 = tensor-core level with TMA-fed A, 4 = levels m-2
+ * and m-1 fused),
  * level d, useful flops of that launch (Tbl. 4 terms of level d; 0 for the
  * split), and its duration in ms.  *count receives the number of records. */
 int sttsm_profile_enable(int on);

@@ -117,6 +117,8 @@ def _load():
     L.sttsm_serve_destroy.restype = i32
     L.sttsm_set_small_kernel.argtypes = [i32]
     L.sttsm_set_small_kernel.restype = i32
+    L.sttsm_set_fused_tail.argtypes = [i32]
+    L.sttsm_set_fused_tail.restype = i32
     L.sttsm_bcss_noalloc.argtypes = [P, P, i32, i64, i64, i32, P, i32, P]
     L.sttsm_bcss_noalloc.restype = i32
     L.sttsm_noalloc_selftest_wait_timeout.argtypes = [ctypes.c_double]
@@ -127,6 +129,8 @@ def _load():
     L.sttsm_profile_read.restype = i32
     L.sttsm_plan_level.argtypes = [i32, i64, i64, i32, i32, i32, P, i64, P, i64, P, P, P]
     L.sttsm_plan_level.restype = i32
+    L.sttsm_plan_pair.argtypes = [i32, i64, i64, i32, P, i64, P, P]
+    L.sttsm_plan_pair.restype = i32
     _lib = L
     return L
 
@@ -139,8 +143,8 @@ def exported_symbols() -> list[str]:
             "sttsm_autotune_b_measured", "sttsm_batch_plan_create", "sttsm_batch_workspace_size",
             "sttsm_batch_info", "sttsm_batch_run", "sttsm_batch_plan_destroy", "sttsm_batch", "sttsm_serve_create",
             "sttsm_serve_submit", "sttsm_serve_poll", "sttsm_serve_stats", "sttsm_serve_destroy",
-            "sttsm_bcss_noalloc", "sttsm_noalloc_selftest_wait_timeout", "sttsm_set_small_kernel", "sttsm_device_status", "sttsm_selftest_wait_timeout",
-            "sttsm_plan_level", "sttsm_profile_enable", "sttsm_profile_read"]
+            "sttsm_bcss_noalloc", "sttsm_noalloc_selftest_wait_timeout", "sttsm_set_small_kernel", "sttsm_set_fused_tail", "sttsm_device_status", "sttsm_selftest_wait_timeout",
+            "sttsm_plan_level", "sttsm_plan_pair", "sttsm_profile_enable", "sttsm_profile_read"]
 
 
 def _check(fn: str, rc: int) -> None:
@@ -434,6 +438,20 @@ def sttsm_set_small_kernel(kind: int) -> None:
     _check("sttsm_set_small_kernel", _load().sttsm_set_small_kernel(kind))
 
 
+FUSED_TAIL_OFF = 0
+FUSED_TAIL_CALLS = 1      # single calls (default)
+FUSED_TAIL_ALL = 2        # batch plans and serving too
+
+
+def sttsm_set_fused_tail(mode: int) -> None:
+    """Short contractions: levels m-2 and m-1 as one launch with T^(1) in shared
+    memory, or as two launches through the workspace (same bits).  mode:
+    FUSED_TAIL_OFF, FUSED_TAIL_CALLS (default), FUSED_TAIL_ALL (True/False map to
+    FUSED_TAIL_CALLS/FUSED_TAIL_OFF)."""
+    mode = {True: FUSED_TAIL_CALLS, False: FUSED_TAIL_OFF}.get(mode, mode) if isinstance(mode, bool) else int(mode)
+    _check("sttsm_set_fused_tail", _load().sttsm_set_fused_tail(mode))
+
+
 def sttsm_selftest_wait_timeout(limit_ms: float) -> int:
     """Runs the bounded-wait self-test; returns the status code (STTSM_ERR_TIMEOUT expected)."""
     return int(_load().sttsm_selftest_wait_timeout(float(limit_ms)))
@@ -459,6 +477,18 @@ def sttsm_plan_level(m: int, n: int, p: int, b: int, prec: int, d: int):
     return tiles, G, dict(zip(keys, [int(v) for v in info]))
 
 
+def sttsm_plan_pair(m: int, n: int, p: int, b: int):
+    """Units of the fused last-two-levels launch: (tiles [ntiles x 8] int32, tuples per
+    unit); raises SttsmError (STTSM_ERR_UNSUPPORTED) for shapes that do not take it."""
+    import numpy as np
+    L = _load()
+    nt, g = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check("sttsm_plan_pair", L.sttsm_plan_pair(m, n, p, b, None, 0, ctypes.byref(nt), ctypes.byref(g)))
+    tiles = np.zeros((nt.value, 8), dtype=np.int32)
+    _check("sttsm_plan_pair", L.sttsm_plan_pair(m, n, p, b, tiles.ctypes.data, nt.value, None, None))
+    return tiles, int(g.value)
+
+
 def sttsm_profile_enable(on: bool) -> None:
     _check("sttsm_profile_enable", _load().sttsm_profile_enable(1 if on else 0))
 
@@ -476,7 +506,7 @@ def sttsm_profile_read() -> list[dict]:
     ms = np.zeros(n, dtype=np.float32)
     _check("sttsm_profile_read", L.sttsm_profile_read(n, kind.ctypes.data, level.ctypes.data, flops.ctypes.data,
                                                       ms.ctypes.data, ctypes.byref(cnt)))
-    names = {0: "fp64", 1: "tc", 2: "split", 3: "tma"}
+    names = {0: "fp64", 1: "tc", 2: "split", 3: "tma", 4: "pair"}
     return [dict(kind=names[int(k)], level=int(l), useful_flops=float(f), ms=float(t))
             for k, l, f, t in zip(kind, level, flops, ms)]
 

@@ -15,7 +15,7 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "_lib" / "libsttsm.so"
 SOURCES = ["plan.cu", "capi.cu", "kernels_simt.cu", "kernels_tc.cu", "noalloc.cu", "batch.cu", "serve.cu", "kernels_tma.cu",
-           "autotune.cu"]
+           "autotune.cu", "kernels_pair.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I" + str(ROOT / "include"), "-I" + str(CSRC)]

@@ -68,6 +68,7 @@ double plan_cost(const Shape& s, int prec, int BM, int BN)
 struct Instance {
     sttsm_desc desc;
     Shape shape;
+    bool fused = false;         // last two levels in the fused launch
     size_t ws_bytes;
     size_t x_off, buf_off[2];   // offsets inside the instance's workspace slice
     int rows, Kp;
@@ -88,6 +89,7 @@ struct Wave {
     SplitDesc* d_split = nullptr;
     int split_blocks = 0;
     LevelLaunch lv[STTSM_MAX_M][2];   // [level][0: regular tiles, 1: small-tile kernel]
+    LevelLaunch pair;                  // fused last two levels of the short contractions, after every level
 };
 
 }  // namespace
@@ -119,6 +121,8 @@ void destroy_plan(sttsm_batch_plan_s* P)
                 if (w.lv[d][k].d_tiles) cudaFree(w.lv[d][k].d_tiles);
                 if (w.lv[d][k].d_insts) cudaFree(w.lv[d][k].d_insts);
             }
+        if (w.pair.d_tiles) cudaFree(w.pair.d_tiles);
+        if (w.pair.d_insts) cudaFree(w.pair.d_insts);
     }
     for (auto& kv : P->G) cudaFree(kv.second);
     if (P->exec) cudaGraphExecDestroy(P->exec);
@@ -161,9 +165,12 @@ int bind_workspace(sttsm_batch_plan_s* P, char* ws)
         // position of every instance in the wave
         std::map<int, size_t> pos;
         for (size_t a = 0; a < w.ids.size(); ++a) pos[w.ids[a]] = a;
-        for (int d = 0; d < w.max_m; ++d)
+        for (int d = 0; d <= w.max_m; ++d)
         for (int mode = 0; mode < 2; ++mode) {
-            LevelLaunch& L = w.lv[d][mode];
+            // d == w.max_m: the pair launch (each instance at its own level m - 2)
+            const bool pairl = d == w.max_m;
+            if (pairl && mode == 1) continue;
+            LevelLaunch& L = pairl ? w.pair : w.lv[d][mode];
             if (L.inst_ids.empty()) continue;
             std::vector<TcInst> tci(L.inst_ids.size());
             std::vector<LevelInst> lvi(L.inst_ids.size());
@@ -171,14 +178,15 @@ int bind_workspace(sttsm_batch_plan_s* P, char* ws)
                 const int id = L.inst_ids[e];
                 const Instance& I = P->inst[id];
                 const Shape& s = I.shape;
-                const LevelShape& LS = s.lv[d];
+                const int dl = pairl ? s.m - 2 : d;
+                const LevelShape& LS = s.lv[dl];
                 char* base = ws + w.ws_off[pos[id]];
                 LevelInst li;
                 memset(&li, 0, sizeof(li));
-                li.parent = d == 0 ? I.desc.A : (const void*)(base + I.buf_off[(d - 1) & 1]);
-                li.out = d == s.m - 1 ? I.desc.C : (void*)(base + I.buf_off[d & 1]);
-                li.G = P->G.at(std::make_tuple(s.m, s.nbar, s.b, d));
-                li.OFF = li.G + level_G_size(s, d);
+                li.parent = dl == 0 ? I.desc.A : (const void*)(base + I.buf_off[(dl - 1) & 1]);
+                li.out = (dl == s.m - 1 || pairl) ? I.desc.C : (void*)(base + I.buf_off[dl & 1]);
+                li.G = P->G.at(std::make_tuple(s.m, s.nbar, s.b, dl));
+                li.OFF = li.G + level_G_size(s, dl);
                 li.X = I.desc.X;
                 li.m = s.m; li.b = s.b; li.k = LS.k; li.nbar = (int32_t)s.nbar;
                 li.n = (int32_t)s.n; li.p = (int32_t)s.p;
@@ -228,6 +236,9 @@ int enqueue(sttsm_batch_plan_s* P, cudaStream_t s)
                                 : launch_level_tc(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, s);
             if (rc != 0) return STTSM_ERR_CUDA;
         }
+        if (w.pair.ntiles > 0 &&
+            launch_level_pair_f32_tc((const TcInst*)w.pair.d_insts, w.pair.d_tiles, w.pair.ntiles, sms, s) != 0)
+            return STTSM_ERR_CUDA;
     }
     return STTSM_OK;
 }
@@ -288,6 +299,7 @@ int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_
         I.buf_off[1] = off;
         off += up256((size_t)s.buf_elems[1] * esz);
         I.ws_bytes = std::max<size_t>(off, 256);
+        I.fused = !fp64 && tc_small_mode(s) && small_kernel_kind() == 0 && fused_tail_in_batches() && pair_mode(s);
         I.cost = sttsm_flops(s.m, s.n, s.p, s.b);
         P->useful_flops += I.cost;
         if (ws_budget && I.ws_bytes > ws_budget) return STTSM_ERR_NOMEM;
@@ -334,12 +346,28 @@ int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_
                 if (I.shape.m <= lv) continue;
                 const bool small = !fp64 && tc_small_mode(I.shape);
                 if ((int)small != mode) continue;
+                if (I.fused && lv >= I.shape.m - 2) continue;   // in the pair launch
                 const int32_t e = (int32_t)L.inst_ids.size();
                 L.inst_ids.push_back(id);
                 build_level_tiles(I.shape, lv, BM, small ? TC_SMALL_BN : BN, e, tiles);
             }
             L.ntiles = (int)tiles.size();
             if (L.ntiles == 0) continue;
+            if (cudaMalloc(&L.d_tiles, tiles.size() * sizeof(Tile)) != cudaSuccess) return STTSM_ERR_NOMEM;
+            if (cudaMemcpy(L.d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess)
+                return STTSM_ERR_CUDA;
+        }
+        LevelLaunch& L = w.pair;
+        std::vector<Tile> tiles;
+        for (int id : w.ids) {
+            const Instance& I = P->inst[id];
+            if (!I.fused) continue;
+            const int32_t e = (int32_t)L.inst_ids.size();
+            L.inst_ids.push_back(id);
+            build_pair_tiles(I.shape, e, tiles);
+        }
+        L.ntiles = (int)tiles.size();
+        if (L.ntiles > 0) {
             if (cudaMalloc(&L.d_tiles, tiles.size() * sizeof(Tile)) != cudaSuccess) return STTSM_ERR_NOMEM;
             if (cudaMemcpy(L.d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess)
                 return STTSM_ERR_CUDA;

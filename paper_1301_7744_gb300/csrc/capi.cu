@@ -144,6 +144,9 @@ namespace sttsm {
 
 std::atomic<int> g_small_kind{0};
 int small_kernel_kind() { return g_small_kind.load(); }
+std::atomic<int> g_fused_tail{1};
+bool fused_tail_enabled() { return g_fused_tail.load() != 0; }
+bool fused_tail_in_batches() { return g_fused_tail.load() == 2; }
 
 int* batch_status_word() { return status_dev(); }
 int peek_status_word() { return g_status_host ? __atomic_load_n(g_status_host, __ATOMIC_SEQ_CST) : 0; }
@@ -335,6 +338,13 @@ int sttsm_set_small_kernel(int kind)
     return STTSM_OK;
 }
 
+int sttsm_set_fused_tail(int mode)
+{
+    if (mode < 0 || mode > 2) return STTSM_ERR_ARG;
+    g_fused_tail.store(mode);
+    return STTSM_OK;
+}
+
 int sttsm_profile_enable(int on)
 {
     std::lock_guard<std::mutex> lock(g_prof_mu);
@@ -389,6 +399,24 @@ int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_
     if (G) {
         if (G_cap < (int64_t)g.size()) return STTSM_ERR_NOMEM;
         memcpy(G, g.data(), g.size() * sizeof(int32_t));
+    }
+    return STTSM_OK;
+}
+
+int sttsm_plan_pair(int m, int64_t n, int64_t p, int b, int32_t* tiles, int64_t tiles_cap, int64_t* ntiles_out,
+                    int32_t* group_out)
+{
+    Shape s;
+    int rc = make_shape(m, n, p, b, &s);
+    if (rc != STTSM_OK) return rc;
+    if (!pair_mode(s)) return STTSM_ERR_UNSUPPORTED;
+    std::vector<Tile> tl;
+    build_pair_tiles(s, 0, tl);
+    if (ntiles_out) *ntiles_out = (int64_t)tl.size();
+    if (group_out) *group_out = pair_group(s);
+    if (tiles) {
+        if (tiles_cap < (int64_t)tl.size()) return STTSM_ERR_NOMEM;
+        memcpy(tiles, tl.data(), tl.size() * sizeof(Tile));
     }
     return STTSM_OK;
 }
@@ -481,11 +509,14 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
         rc = make_x_tensor_map(&ti.tmX, ws + w.xpieces, np, w.rows, w.Kp, BN);
         if (rc != STTSM_OK) return rc;
     }
+    // short contractions in FP32: the last two levels in one launch, T^(1) in shared memory
+    const bool pair = small && small_kernel_kind() == 0 && fused_tail_enabled() && nlev == m && P->d_pair;
     for (int d = 0; d < nlev; ++d) {
         const LevelShape& LS = s.lv[d];
         LevelInst& L = ti.L;
+        const bool fused = pair && d == m - 2;
         L.parent = d == 0 ? A : bufs[(d - 1) & 1];
-        L.out = d == nlev - 1 ? C : bufs[d & 1];
+        L.out = (d == nlev - 1 || fused) ? C : bufs[d & 1];
         L.G = P->d_G[d];
         L.OFF = P->d_G[d] + level_G_size(s, d);
         L.X = X;
@@ -499,7 +530,15 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
         L.rows_per_parent = LS.P_out * s.R;
         int64_t bp = 1;
         for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
-        const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
+        double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
+        if (fused) {
+            const LevelShape& L2 = s.lv[m - 1];
+            lflops += (double)L2.nodes_out * (double)L2.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
+            ProfScope ps(stream, 4, d, lflops);
+            rc = cuda_err(launch_level_pair_f32(L, nullptr, P->d_pair, P->npair, sms, stream));
+            if (rc != STTSM_OK) return rc;
+            break;   // level m-1 is done too
+        }
         ProfScope ps(stream, fp64 ? 0 : 1, d, lflops);
         if (fp64) rc = cuda_err(launch_level_fp64(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
         else if (small && small_kernel_kind() == 0) rc = cuda_err(launch_level_small_f32(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));

@@ -44,6 +44,16 @@ int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, con
                            int num_sms, cudaStream_t s);
 int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s);
 
+// Levels m-2 and m-1 of short contractions fused (kernels_pair.cu): the
+// descriptor describes level m-2 with out = C; tiles from build_pair_tiles.
+int launch_level_pair_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
+                          int num_sms, cudaStream_t s);
+int launch_level_pair_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s);
+// Whether short contractions run their last two levels fused (sttsm_set_fused_tail):
+// in single calls (mode >= 1), and in batch plans and serving (mode 2).
+bool fused_tail_enabled();
+bool fused_tail_in_batches();
+
 // Kernel for short contractions under the split precisions: 0 = FP32 CUDA-core
 // kernel (default), 1 = tcgen05 small-tile kernel (sttsm_set_small_kernel).
 int small_kernel_kind();

@@ -3,6 +3,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include "launch.h"
 #include "plan.h"
 #include "sttsm.h"
 
@@ -133,6 +134,53 @@ int64_t level_tile_count(const Shape& s, int d, int BM, int BN)
     return count;
 }
 
+int pair_group(const Shape& s)
+{
+    const int64_t Kc = (s.nbar * s.b + 3) & ~(int64_t)3;
+    const int64_t S_total = s.R / s.b;
+    const int64_t g = PAIR_ROWS / Kc;
+    return (int)(g < S_total ? g : S_total);
+}
+
+bool pair_mode(const Shape& s)
+{
+    if (s.m < 2 || s.nbar * s.b > 64 || s.pbar * s.b > 64) return false;
+    const int64_t Kc = (s.nbar * s.b + 3) & ~(int64_t)3;
+    const int64_t Gs = pair_group(s);
+    if (Gs < 1) return false;
+    const int64_t RBp = (s.b * Gs + 3) & ~(int64_t)3;
+    return Kc * s.pbar * RBp <= PAIR_U_MAX;
+}
+
+void build_pair_tiles(const Shape& s, int32_t inst, std::vector<Tile>& tiles)
+{
+    const int d = s.m - 2;
+    const LevelShape& L = s.lv[d];
+    const int Gs = pair_group(s);
+    const int64_t S_total = s.R / s.b;
+    int32_t u[STTSM_MAX_M];
+    for (int64_t par = 0; par < L.nodes_parent; ++par) {
+        int64_t children = s.pbar, cbase = 0;
+        if (d > 0) {
+            colex_unrank(par, d, u);   // J = (jbar_2 <= ... <= jbar_{m-1})
+            children = (int64_t)u[0] + 1;
+            for (int t = 0; t < d; ++t) cbase += binom_small((int64_t)u[t] + t + 2, t + 3);
+        }
+        for (int64_t s0 = 0; s0 < S_total; s0 += Gs) {
+            Tile t;
+            t.inst = inst;
+            t.parent = (int32_t)par;
+            t.child_base = 0;
+            t.row0 = (int32_t)s0;
+            t.col0 = (int32_t)children;
+            t.ncols = Gs;
+            t.pad0 = (int32_t)cbase;
+            t.pad1 = 0;
+            tiles.push_back(t);
+        }
+    }
+}
+
 namespace {
 std::mutex g_mu;
 std::map<std::tuple<int, int, int64_t, int64_t, int, int, int>, DevPlan*> g_plans;
@@ -143,6 +191,7 @@ void free_plan(DevPlan* P)
         if (P->d_tiles[d]) cudaFree(P->d_tiles[d]);
         if (P->d_G[d]) cudaFree(P->d_G[d]);
     }
+    if (P->d_pair) cudaFree(P->d_pair);
     delete P;
 }
 }  // namespace
@@ -157,6 +206,8 @@ const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN)
     if (it != g_plans.end()) return it->second;
     DevPlan* P = new DevPlan();
     for (int d = 0; d < STTSM_MAX_M; ++d) { P->d_tiles[d] = nullptr; P->d_G[d] = nullptr; P->ntiles[d] = 0; P->maxcols[d] = 0; }
+    P->d_pair = nullptr;
+    P->npair = 0;
     if (make_shape(m, n, p, b, &P->shape) != STTSM_OK) { delete P; return nullptr; }
     P->BM = BM;
     P->BN = BN;
@@ -171,6 +222,16 @@ const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN)
             cudaMalloc(&P->d_G[d], G.size() * sizeof(int32_t)) != cudaSuccess ||
             cudaMemcpy(P->d_tiles[d], tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(P->d_G[d], G.data(), G.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+            free_plan(P);
+            return nullptr;
+        }
+    }
+    if (BM == TC_BM && pair_mode(P->shape)) {
+        std::vector<Tile> tiles;
+        build_pair_tiles(P->shape, 0, tiles);
+        P->npair = (int)tiles.size();
+        if (cudaMalloc(&P->d_pair, tiles.size() * sizeof(Tile)) != cudaSuccess ||
+            cudaMemcpy(P->d_pair, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess) {
             free_plan(P);
             return nullptr;
         }

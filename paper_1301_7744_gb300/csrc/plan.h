@@ -56,6 +56,18 @@ int64_t level_tile_count(const Shape& s, int d, int BM, int BN);
 void build_level_G(const Shape& s, int d, std::vector<int32_t>& G);
 inline int64_t level_G_size(const Shape& s, int d) { return s.lv[d].P_out * s.nbar; }
 
+// The last two levels fused (kernels_pair.cu): FP32 short contractions whose
+// contraction and output widths are at most 64 (nbar b <= 64, pbar b <= 64),
+// m >= 2, and whose unit of work (G_s trailing index tuples, Kc G_s <= 128
+// level m-2 rows with Kc = nbar b rounded up to 4) keeps its T^(1) slice of
+// Kc x pbar x (b G_s rounded up to 4) entries within PAIR_U_MAX.
+constexpr int PAIR_U_MAX = 10240;
+constexpr int PAIR_ROWS = 128;
+int pair_group(const Shape& s);          // G_s of the fused units
+bool pair_mode(const Shape& s);
+// Units of the fused launch (fields as kernels_pair.cu reads them), appended.
+void build_pair_tiles(const Shape& s, int32_t inst, std::vector<Tile>& tiles);
+
 struct DevPlan {
     Shape shape;
     int BM, BN;
@@ -63,6 +75,8 @@ struct DevPlan {
     int maxcols[STTSM_MAX_M];   // widest tile of each level
     Tile* d_tiles[STTSM_MAX_M];
     int32_t* d_G[STTSM_MAX_M];
+    Tile* d_pair;               // fused last two levels (pair_mode shapes of the split plans), else nullptr
+    int npair;
 };
 
 // Cached device plan for (shape, tile sizes) on the current device; nullptr

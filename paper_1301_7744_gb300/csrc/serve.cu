@@ -111,6 +111,7 @@ struct Req {
     Shape s;
     bool small = false;
     bool tma = false;           // TMA-fed kernel: A split once into pieces, temporaries as pieces
+    bool fused = false;         // levels m-2 and m-1 in one step (the fused short-contraction kernel)
     size_t a_off = 0;
     int state = Q_QUEUED;
     int level = 0;              // next level to launch
@@ -283,6 +284,14 @@ int admit(sttsm_serve_s* H, Req& R, const TableSet& T)
         L.rows_per_parent = LS.P_out * s.R;
         int64_t bp = 1;
         for (int q = 0; q <= STTSM_MAX_M; ++q) { L.bpow[q] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= s.b; }
+        if (R.fused && d >= s.m - 2) {
+            // levels m-2 and m-1 in one launch: the pair units, writing C
+            R.tiles[d].clear();
+            if (d == s.m - 2) {
+                build_pair_tiles(s, 0, R.tiles[d]);
+                L.out = R.d.C;
+            }
+        }
         if (R.tma) {
             TmaInst& M = R.tinst[d];
             memset(&M, 0, sizeof(M));
@@ -304,9 +313,10 @@ int launch_step(sttsm_serve_s* H)
     std::vector<const Req*> asplit;            // TMA requests whose A is split this step
     // groups: 0 gathered A, 1 small tiles, 2 / 3 TMA writing pieces / C with b a
     // multiple of 32, 4 / 5 the same with b an odd multiple of 16
-    constexpr int NG = 6;
-    std::vector<TcInst> insts[2];
-    std::vector<TmaInst> tinsts[NG - 2];
+    // group 6: the fused last two levels of short contractions
+    constexpr int NG = 7;
+    std::vector<TcInst> insts[3];               // groups 0, 1, 6
+    std::vector<TmaInst> tinsts[4];             // groups 2 .. 5
     std::vector<Tile> tiles[NG];
     std::vector<uint64_t> finishing, stepped, waiting;
     size_t need = 0;
@@ -328,19 +338,26 @@ int launch_step(sttsm_serve_s* H)
             R.split_done = true;
         }
         const bool last = R.level == R.s.m - 1;
-        const int g = R.tma ? (last ? 3 : 2) + (tma_sw32(R.s) ? 2 : 0) : (R.small ? 1 : 0);
+        const bool pairg = R.fused && R.level == R.s.m - 2;
+        const int g = pairg ? 6 : R.tma ? (last ? 3 : 2) + (tma_sw32(R.s) ? 2 : 0) : (R.small ? 1 : 0);
         int32_t e;
-        if (g < 2) { e = (int32_t)insts[g].size(); insts[g].push_back(R.inst[R.level]); }
-        else { e = (int32_t)tinsts[g - 2].size(); tinsts[g - 2].push_back(R.tinst[R.level]); }
+        if (g < 2 || g == 6) {
+            const int ii = g == 6 ? 2 : g;
+            e = (int32_t)insts[ii].size();
+            insts[ii].push_back(R.inst[R.level]);
+        } else {
+            e = (int32_t)tinsts[g - 2].size();
+            tinsts[g - 2].push_back(R.tinst[R.level]);
+        }
         for (Tile t : R.tiles[R.level]) {
             t.inst = e;
             tiles[g].push_back(t);
         }
     }
     // staging layout: [TmaInst 2..5][TcInst 0, 1][tiles 0..5][split]
-    size_t off = 0, o_ti[NG - 2], o_i[2], o_t[NG], o_s;
-    for (int k = 0; k < NG - 2; ++k) { o_ti[k] = off; off = up256(off + tinsts[k].size() * sizeof(TmaInst)); }
-    for (int k = 0; k < 2; ++k) { o_i[k] = off; off = up256(off + insts[k].size() * sizeof(TcInst)); }
+    size_t off = 0, o_ti[4], o_i[3], o_t[NG], o_s;
+    for (int k = 0; k < 4; ++k) { o_ti[k] = off; off = up256(off + tinsts[k].size() * sizeof(TmaInst)); }
+    for (int k = 0; k < 3; ++k) { o_i[k] = off; off = up256(off + insts[k].size() * sizeof(TcInst)); }
     for (int k = 0; k < NG; ++k) { o_t[k] = off; off = up256(off + tiles[k].size() * sizeof(Tile)); }
     o_s = off;
     off = up256(off + split.size() * sizeof(SplitDesc));
@@ -348,9 +365,9 @@ int launch_step(sttsm_serve_s* H)
     if (off > S.cap) return STTSM_ERR_NOMEM;   // cannot happen: requests were taken while they fit
     // the copy that last read this staging buffer (two steps back) has finished
     if (cudaEventSynchronize(S.copied) != cudaSuccess) return STTSM_ERR_CUDA;
-    for (int k = 0; k < NG - 2; ++k)
+    for (int k = 0; k < 4; ++k)
         if (!tinsts[k].empty()) memcpy(S.h + o_ti[k], tinsts[k].data(), tinsts[k].size() * sizeof(TmaInst));
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 3; ++k)
         if (!insts[k].empty()) memcpy(S.h + o_i[k], insts[k].data(), insts[k].size() * sizeof(TcInst));
     for (int k = 0; k < NG; ++k)
         if (!tiles[k].empty()) memcpy(S.h + o_t[k], tiles[k].data(), tiles[k].size() * sizeof(Tile));
@@ -375,6 +392,7 @@ int launch_step(sttsm_serve_s* H)
         if (k == 0) lrc = launch_level_tc(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, H->stream);
         else if (k == 1 && small_kernel_kind() == 0) lrc = launch_level_small_f32_tc((const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->stream);
         else if (k == 1) lrc = launch_level_tc_small(H->np, dummy, (const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->status, H->stream);
+        else if (k == 6) lrc = launch_level_pair_f32_tc((const TcInst*)(S.d + o_i[2]), dt, n, H->sms, H->stream);
         else {
             int maxc = 0;
             for (const Tile& t : tiles[k]) maxc = std::max(maxc, (int)t.ncols);
@@ -389,7 +407,8 @@ int launch_step(sttsm_serve_s* H)
     std::vector<uint64_t> still = waiting;
     for (uint64_t tk : stepped) {
         Req& R = H->reqs[tk];
-        if (++R.level == R.s.m) {
+        R.level += (R.fused && R.level == R.s.m - 2) ? 2 : 1;
+        if (R.level == R.s.m) {
             R.state = Q_FINISHING;
             finishing.push_back(tk);
         } else {
@@ -554,6 +573,7 @@ int sttsm_serve_submit(void* h, const sttsm_desc* d, uint64_t* ticket)
     if (rc != STTSM_OK) return rc;
     R.small = tc_small_mode(R.s);
     R.tma = tc_tma_mode(R.s);
+    R.fused = R.small && small_kernel_kind() == 0 && fused_tail_in_batches() && pair_mode(R.s);
     R.rows = (int)(R.s.pbar * R.s.b);
     R.Kp = (int)(((R.s.nbar * R.s.b) + 7) / 8 * 8);
     R.x_off = 0;

@@ -115,3 +115,25 @@ def test_one_shot_batch(st):
     st.sttsm_batch(insts, prec, ws)
     for (Ab, dX, C, m, n, p, b), (A, X) in zip(insts, host):
         assert rel_fro(C.double().cpu().numpy(), oracle_C_bcss(A, X, m, p, b)) <= 1e-6
+
+
+def test_batch_fused_tail_equals_two_launches(st):
+    """A batch whose short instances run their last two levels fused gives the same
+    bits as the same batch planned with the fused launch switched off."""
+    prec, insts, host = make_batch(st, 48, 5, False)
+    outs = []
+    for fused in (st.FUSED_TAIL_ALL, st.FUSED_TAIL_OFF):
+        st.sttsm_set_fused_tail(fused)
+        try:
+            plan = st.BatchPlan(insts, prec)
+            ws = torch.empty(max(plan.workspace_size(), 1), dtype=torch.uint8, device="cuda")
+            for (_, _, C, *_rest) in insts:
+                C.fill_(float("nan"))
+            plan.run(ws)
+            torch.cuda.synchronize()
+            outs.append([C.double().cpu().numpy() for (_, _, C, *_rest) in insts])
+            plan.destroy()
+        finally:
+            st.sttsm_set_fused_tail(st.FUSED_TAIL_CALLS)
+    for a, b in zip(*outs):
+        assert not np.isnan(a).any() and np.array_equal(a, b)

@@ -423,3 +423,31 @@ def test_measured_autotune(st, precname, cands):
     b2, none = st.sttsm_autotune_b_measured(3, 200, 180, prec, cands, reps=2, with_times=False)
     assert b2 == b and none is None
     assert st.sttsm_device_status() == 0
+
+
+FUSED_SHAPES = [(3, 24, 24, 8), (3, 17, 5, 6), (4, 13, 9, 4), (5, 16, 16, 8), (6, 6, 5, 2), (5, 37, 29, 4),
+                (3, 40, 12, 1), (2, 30, 20, 1), (4, 21, 21, 7), (3, 64, 64, 16), (2, 40, 50, 4), (4, 5, 1, 2)]
+
+
+@pytest.mark.parametrize("m,n,p,b", FUSED_SHAPES)
+def test_fused_last_two_levels(st, m, n, p, b):
+    """Short contractions run levels m-2 and m-1 in one launch with T^(1) in shared
+    memory: the same bits as the two launches through the workspace, and the
+    oracle's C within the split-path tolerance."""
+    A, X = inputs(m, n, p, seed_a=5 * m + n, seed_x=p + 1, fp32=True)
+    Ab = device_bcss_from_dense(st, A, m, n, b, torch.float32)
+    st.sttsm_profile_enable(True)
+    try:
+        fused = run_sttsm(st, Ab, X, m, n, p, b, st.STTSM_BF16X6)
+        kinds = [r["kind"] for r in st.sttsm_profile_read() if r["kind"] != "split"]
+    finally:
+        st.sttsm_profile_enable(False)
+    assert kinds.count("pair") == 1 and len(kinds) == m - 1, kinds
+    st.sttsm_set_fused_tail(False)
+    try:
+        two = run_sttsm(st, Ab, X, m, n, p, b, st.STTSM_BF16X6)
+    finally:
+        st.sttsm_set_fused_tail(True)
+    assert np.array_equal(fused, two)
+    ref = oracle_C_bcss(A, X, m, p, b)
+    assert rel_fro(fused, ref) <= TOL["bf16x6"] and rel_max(fused, ref) <= TOL["bf16x6"]

@@ -107,3 +107,79 @@ def test_tile_columns_stay_within_x_rows(st):
         for k in np.unique(key)[:200]:
             w = tiles[key == k, 5]
             assert w.sum() == ((tiles[key == k, 4] + w).max()) and (len(w) == 1 or w[:-1].min() >= w.max() - 16)
+
+
+def emulate_pair(st, m, n, p, b, parent, X):
+    """The fused last two levels as the pair kernel addresses them: for every unit
+    (J, trailing tuples s0 .. s0 + G_s - 1) gather the level m-2 rows through
+    level m-2's G and offsets, form U = rows x X^T over all children of J, then
+    C[(jb0, jb1, J)][j0 + b j1 + b^2 s] = sum_i0 X[j0g, i0g] U[i0g, j1g, s]."""
+    nbar, pbar = -(-n // b), -(-p // b)
+    Kt = nbar * b
+    Xpad = np.zeros((pbar * b, Kt))
+    Xpad[:p, :n] = X
+    units, Gs = st.sttsm_plan_pair(m, n, p, b)
+    _, G, info = st.sttsm_plan_level(m, n, p, b, st.STTSM_BF16X6, m - 2)
+    k, R, bm, P_par, P_out = info["k"], info["R"], info["bm"], info["P_parent"], info["P_out"]
+    assert k == 1 and P_out == nbar
+    OFF = G[P_out * nbar:].reshape(k + 1, R)
+    G = G[: P_out * nbar].reshape(P_out, nbar)
+    S_total = R // b
+    assert ((Kt + 3) // 4 * 4) * Gs <= 128
+    nC = st.bcss_num_elems(m, p, b)
+    C = np.zeros(nC)
+    count = np.zeros(nC, dtype=np.int64)
+    kk = np.arange(Kt)
+    ib, a = kk // b, kk % b
+    for inst, par, _, s0, children, gs, cbase, _ in units:
+        assert inst == 0 and gs == Gs and 0 <= par < info["nodes_parent"]
+        s = s0 + np.arange(Gs)
+        s = s[s < S_total]
+        i0g = np.arange(Kt)
+        pr = np.repeat(i0g // b, s.size).reshape(Kt, s.size)
+        rr = (i0g % b)[:, None] + b * s[None, :]
+        gq = G[pr[..., None], ib[None, None, :]]
+        q, rank = gq & 7, gq >> 3
+        off = OFF[q, rr[..., None]] + a[None, None, :] * b ** q
+        idx = (par * P_par + rank) * bm + off
+        assert idx.min() >= 0 and idx.max() < parent.size
+        rows = parent[idx]                                   # [i0g, s, kk]
+        NA = children * b
+        U = np.einsum("isk,jk->ijs", rows, Xpad[:NA])          # [i0g, j1g, s]
+        for jb1 in range(children):
+            for j1 in range(b):
+                Cv = Xpad[: (jb1 + 1) * b] @ U[:, jb1 * b + j1, :]   # [j0g, s]
+                j0g = np.arange((jb1 + 1) * b)
+                node = cbase + jb1 * (jb1 + 1) // 2 + j0g // b
+                cidx = node[:, None] * bm + (j0g % b)[:, None] + b * j1 + b * b * s[None, :]
+                assert cidx.min() >= 0 and cidx.max() < nC
+                C[cidx] = Cv
+                np.add.at(count, cidx.reshape(-1), 1)
+    assert np.all(count == 1), "every C entry is written exactly once"
+    return C
+
+
+PAIR_CASES = [(3, 24, 24, 8), (2, 9, 11, 3), (3, 17, 5, 6), (4, 13, 9, 4), (5, 7, 6, 2), (4, 20, 12, 5),
+              (3, 40, 40, 4), (3, 40, 12, 1), (2, 30, 20, 1), (4, 21, 21, 7), (5, 16, 16, 8), (6, 6, 5, 2),
+              (3, 64, 48, 16), (3, 5, 3, 8), (3, 1, 6, 4), (4, 5, 1, 2)]
+
+
+@pytest.mark.parametrize("m,n,p,b", PAIR_CASES)
+def test_fused_pair_emulation_matches_oracle(st, m, n, p, b):
+    A = synth.sym_uniform_dense(m, n, 17)
+    X = synth.x_gaussian(18, p, n)
+    A_bcss = oracle.bcss_pack(A, m, n, b)
+    parent = A_bcss if m == 2 else emulate(st, m, n, p, b, st.STTSM_BF16X6, A_bcss, X, nlev=m - 2)
+    C_emu = emulate_pair(st, m, n, p, b, parent, X)
+    C_ref = oracle.bcss_pack(oracle.sttsm_chain(A, X, m), m, p, b)
+    assert np.linalg.norm(C_emu - C_ref) <= 1e-12 * np.linalg.norm(C_ref)
+
+
+def test_fused_pair_only_for_short_shapes(st):
+    with pytest.raises(st.SttsmError) as e:
+        st.sttsm_plan_pair(3, 96, 96, 32)
+    assert e.value.code == st.STTSM_ERR_UNSUPPORTED
+    with pytest.raises(st.SttsmError):
+        st.sttsm_plan_pair(3, 40, 90, 4)          # p-bar b > 64
+    with pytest.raises(st.SttsmError):
+        st.sttsm_plan_pair(1, 10, 7, 4)           # one level: nothing to fuse

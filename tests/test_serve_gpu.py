@@ -205,3 +205,25 @@ def test_full_size_classes_sampled_against_oracle(st):
         del A
         vals = np.array([got[bcss_pos(j, m, b)] for j in J])
         assert rel_fro(vals, ref) <= 1e-6 and rel_max(vals, ref) <= 1e-6, (m, n, p, b)
+
+
+def test_fused_tail_in_serving_equals_two_launches(st):
+    """With the fused last two levels switched on for serving (mode 2), short requests
+    finish in m - 1 steps and give the same bits as with two launches."""
+    reqs = requests(st, 8, 7)
+    torch.cuda.synchronize()
+    outs = []
+    for mode in (st.FUSED_TAIL_ALL, st.FUSED_TAIL_OFF):
+        st.sttsm_set_fused_tail(mode)
+        try:
+            srv = st.Server(2 << 30)
+            for r in reqs:
+                r["C"].fill_(float("nan"))
+            tickets = [srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"]) for r in reqs]
+            wait_all(srv, tickets)
+            srv.destroy()
+            outs.append([r["C"].double().cpu().numpy() for r in reqs])
+        finally:
+            st.sttsm_set_fused_tail(st.FUSED_TAIL_CALLS)
+    for a, b in zip(*outs):
+        assert not np.isnan(a).any() and np.array_equal(a, b)
