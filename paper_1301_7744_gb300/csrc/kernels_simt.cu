@@ -3,6 +3,7 @@
 // algorithm-by-blocks (Fig. 5 with Thm. 1).
 #include <cuda_bf16.h>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 #include "common.cuh"
 #include "launch.h"
@@ -40,9 +41,38 @@ __device__ __forceinline__ void bcss_pack_range(const T* __restrict__ dense, T* 
     }
 }
 
+// The same with V consecutive entries per thread (one 16-byte load and store):
+// when b and n are multiples of V, entries e .. e + V - 1 (e a multiple of V)
+// share every index but i_0 and are V consecutive dense entries, all inside
+// or all outside the tensor.
+template <typename T, int V, typename IT>
+__device__ __forceinline__ void bcss_pack_range_vec(const T* __restrict__ dense, T* __restrict__ dst,
+                                                    const int32_t* tup, int m, int64_t n, int b, int lb, IT e0, IT e1)
+{
+    using W = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+#pragma unroll 2
+    for (IT e = e0 + (IT)threadIdx.x * V; e < e1; e += (IT)blockDim.x * V) {
+        IT r = e;
+        int64_t off = 0, stride = 1;
+        bool inside = true;
+        for (int a = 0; a < m; ++a) {
+            const IT q = lb >= 0 ? (IT)(r >> lb) : r / (IT)b;
+            const int64_t i = (int64_t)tup[a] * b + (int64_t)(r - q * (IT)b);
+            r = q;
+            inside = inside && (i < n);
+            off += i * stride;
+            stride *= n;
+        }
+        W v;
+        if (inside) v = *(const W*)(dense + off);
+        else memset(&v, 0, sizeof(v));
+        *(W*)(dst + e) = v;
+    }
+}
+
 template <typename T>
 __global__ void bcss_pack_kernel(const T* __restrict__ dense, T* __restrict__ bcss, int m, int64_t n, int b,
-                                 int64_t nblocks, int64_t bm)
+                                 int64_t nblocks, int64_t bm, int vec)
 {
     __shared__ int32_t tup[STTSM_MAX_M];
     const int64_t nchunk = (bm + PACK_CHUNK - 1) / PACK_CHUNK;
@@ -54,8 +84,15 @@ __global__ void bcss_pack_kernel(const T* __restrict__ dense, T* __restrict__ bc
         if (threadIdx.x == 0) colex_unrank(blk, m, tup);
         __syncthreads();
         T* dst = bcss + blk * bm;
-        if (bm < ((int64_t)1 << 31)) bcss_pack_range<T, uint32_t>(dense, dst, tup, m, n, b, lb, (uint32_t)c0, (uint32_t)c1);
-        else bcss_pack_range<T, int64_t>(dense, dst, tup, m, n, b, lb, c0, c1);
+        constexpr int V = 16 / sizeof(T);
+        if (vec && bm < ((int64_t)1 << 31))
+            bcss_pack_range_vec<T, V, uint32_t>(dense, dst, tup, m, n, b, lb, (uint32_t)c0, (uint32_t)c1);
+        else if (vec)
+            bcss_pack_range_vec<T, V, int64_t>(dense, dst, tup, m, n, b, lb, c0, c1);
+        else if (bm < ((int64_t)1 << 31))
+            bcss_pack_range<T, uint32_t>(dense, dst, tup, m, n, b, lb, (uint32_t)c0, (uint32_t)c1);
+        else
+            bcss_pack_range<T, int64_t>(dense, dst, tup, m, n, b, lb, c0, c1);
     }
 }
 
@@ -141,8 +178,14 @@ int launch_bcss_pack(const void* dense, void* bcss, int m, int64_t n, int b, int
     int threads = bm >= 256 ? 256 : (bm >= 64 ? 64 : 32);
     const int64_t work = nblocks * ((bm + PACK_CHUNK - 1) / PACK_CHUNK);
     int64_t g = work < 152 * 64 ? work : 152 * 64;
-    if (dtype == 0) bcss_pack_kernel<double><<<(int)g, threads, 0, s>>>((const double*)dense, (double*)bcss, m, n, b, nblocks, bm);
-    else bcss_pack_kernel<float><<<(int)g, threads, 0, s>>>((const float*)dense, (float*)bcss, m, n, b, nblocks, bm);
+    // 16-byte accesses: V = 4 floats or 2 doubles per thread when b and n are
+    // multiples of V and both arrays are 16-byte aligned (chunks are multiples of V)
+    const int V = dtype == 0 ? 2 : 4;
+    const int vec = (b % V == 0 && n % V == 0 && ((uintptr_t)dense & 15) == 0 && ((uintptr_t)bcss & 15) == 0) ? 1 : 0;
+    if (dtype == 0)
+        bcss_pack_kernel<double><<<(int)g, threads, 0, s>>>((const double*)dense, (double*)bcss, m, n, b, nblocks, bm, vec);
+    else
+        bcss_pack_kernel<float><<<(int)g, threads, 0, s>>>((const float*)dense, (float*)bcss, m, n, b, nblocks, bm, vec);
     return (int)cudaGetLastError();
 }
 

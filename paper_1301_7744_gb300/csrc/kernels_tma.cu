@@ -166,6 +166,12 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 const int pr = t.row0 / I.R, rr0 = t.row0 - pr * I.R;
                 const int32_t* Grow = I.G + (int64_t)pr * I.nbar;
                 const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
+                // 16-wide slices: running (stored block, offset in it) and the insertion
+                // positions whose runs are loaded atom by atom
+                int sl_ib = 0, sl_a = 0;
+                uint32_t amask = 0;
+                if (SW32)
+                    for (int q = 1; q <= I.k; ++q) amask |= atomwise_run(I.bpow[q]) ? (1u << q) : 0u;
                 for (int ks = 0; ks < nk; ++ks) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                     const int k0 = ks * TC_KC;
@@ -181,8 +187,9 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                         const int nsl = k0 + 16 < I.Ktot ? 2 : 1;
                         mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(nsl * NP * (S::A_PLANE / 2)) + x_bytes);
                         for (int h = 0; h < nsl; ++h) {
-                            const int k = k0 + 16 * h;
-                            const int ib = k / I.b, a0 = k - ib * I.b;
+                            const int ib = sl_ib, a0 = sl_a;
+                            sl_a += 16;
+                            if (sl_a == I.b) { sl_a = 0; ++sl_ib; }
                             const int32_t gq = __ldg(Grow + ib);
                             const int q = gq & 7;
                             const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
@@ -191,7 +198,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                                 tma_load_3d(dA, &TI.tmA[0], a0, rr0, bp, full_bar(stage));
                             } else {
                                 const int bq = I.bpow[q];
-                                if (atomwise_run(bq)) {
+                                if ((amask >> q) & 1u) {
                                     // 16-row atoms one by one (each lies inside one run of
                                     // b^q contiguous rows), all pieces of an atom together
 #pragma unroll 1
@@ -251,17 +258,22 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 if (!mbar_wait(d1_empty, tile_phase ^ 1u, abort_flag, status)) { ok = false; break; }
                 tile_phase ^= 1u;
                 tc_fence_after();
+                int sl_ib = 0, sl_a = 0;
+                uint32_t amask = 0;
+                if (SW32)
+                    for (int q = 1; q <= I.k; ++q) amask |= atomwise_run(I.bpow[q]) ? (1u << q) : 0u;
                 for (int ks = 0; ks < nk; ++ks) {
                     // A major-ness, atom layout and presence of the two 16-wide K slices
                     bool mnk[2], valid[2], atom[2];
                     if (SW32) {
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const int k = ks * TC_KC + 16 * h;
-                            valid[h] = k < I.Ktot;
-                            const int q = valid[h] ? (__ldg(Grow + k / I.b) & 7) : 0;
+                            valid[h] = ks * TC_KC + 16 * h < I.Ktot;
+                            const int q = valid[h] ? (__ldg(Grow + sl_ib) & 7) : 0;
                             mnk[h] = q != 0;
-                            atom[h] = q != 0 && atomwise_run(I.bpow[q]);
+                            atom[h] = ((amask >> q) & 1u) != 0;
+                            sl_a += 16;
+                            if (sl_a == I.b) { sl_a = 0; ++sl_ib; }
                         }
                     } else {
                         const int ib = (ks * TC_KC) / I.b;
