@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--b", default="auto", help="block size or 'auto'")
-    ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16x6_r64", "bf16x3_r64"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
     ap.add_argument("--workload", default="single", choices=["single", "m4", "abo", "batch", "serve"],
@@ -81,6 +81,11 @@ def peaks():
         return d, "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def prec_code(st, name):
+    return {"bf16x6": st.STTSM_BF16X6, "bf16x3": st.STTSM_BF16X3, "bf16x6_r64": st.STTSM_BF16X6_R64,
+            "bf16x3_r64": st.STTSM_BF16X3_R64}[name]
 
 
 def tensor_peak(pk, pk_src, clk, timed_ms):
@@ -443,7 +448,7 @@ def fp64_path(st, torch, Xh, b, F, ms):
              "library_fp64_gemm_tflops": dgemm, "frac_of_library_fp64_gemm": value / dgemm}, C64)
 
 
-def check_and_baseline(args, C, C64, Xh, X32, b, F, world):
+def check_and_baseline(args, C, C64, Xh, X32, b, F, world, C_r64=None):
     """Sampled relative error of both paths against the FP64 oracle, and the
     oracle itself timed on this host's cores (N = 1 only)."""
     import oracle
@@ -457,6 +462,11 @@ def check_and_baseline(args, C, C64, Xh, X32, b, F, world):
     rel_err = {"samples": 256, args.prec: float(np.linalg.norm(got32 - ref32) / np.linalg.norm(ref32)),
                "tolerance": {args.prec: 1e-6, "fp64": 1e-12},
                "elementwise": {args.prec: float(np.max(np.abs(got32 - ref32)) / np.max(np.abs(ref32)))}}
+    if C_r64 is not None:
+        cr = C_r64.double().cpu().numpy()
+        gotr = np.array([cr[bcss_pos(j, b)] for j in J])
+        rel_err["bf16x6_r64"] = float(np.linalg.norm(gotr - ref32) / np.linalg.norm(ref32))
+        rel_err["elementwise"]["bf16x6_r64"] = float(np.max(np.abs(gotr - ref32)) / np.max(np.abs(ref32)))
     if C64 is not None:
         ref64 = oracle.sttsm_entries(A_dense, Xh, M, J)
         c64 = C64.cpu().numpy()
@@ -581,7 +591,7 @@ def run_abo(args):
     import synth
     import oracle
     b = 64 if args.b == "auto" else int(args.b)
-    prec = st.STTSM_BF16X6 if args.prec == "bf16x6" else st.STTSM_BF16X3
+    prec = prec_code(st, args.prec)
     Xh = synth.x_gaussian(SEED_X, P, N)
     X32 = Xh.astype(np.float32).astype(np.float64)
     dX = torch.from_numpy(xcol32(Xh)).cuda()
@@ -780,7 +790,7 @@ def run_batch(args, emit=True, short=False):
 SERVE_B = {3: (16, 32, 64), 4: (8, 16, 32), 5: (4, 8, 16), 6: (4, 8)}
 
 
-def run_serve(args, emit=True, seconds=None):
+def run_serve(args, emit=True, seconds=None, serve_prec=None):
     """Serving workload: Poisson arrivals (rate, seconds), uniform over the classes
     m=3 (n,p in [64,512]), m=4 ([32,160]), m=5 ([16,64]), m=6 ([8,32]); BF16X6; the
     server admits by HBM budget and batches continuously.  Inputs come from a pool of
@@ -792,7 +802,7 @@ def run_serve(args, emit=True, seconds=None):
     import paper_1301_7744_gb300 as st
     st.sttsm_set_fused_tail(args.fused_tail)
     import synth
-    prec = st.STTSM_BF16X6
+    prec = prec_code(st, serve_prec or "bf16x6")
     seconds = float(seconds or args.serve_seconds)
     reqs = synth.serve_requests(4, args.serve_rate, seconds)
     pool_n, cbuf = 32, 8
@@ -895,7 +905,7 @@ def run_serve(args, emit=True, seconds=None):
     line = {"metric": "sttsm serving latency p50/p99 (ms) and throughput, Poisson %.0f req/s for %.0f s"
                       % (args.serve_rate, seconds),
             "value": float(np.percentile(lat, 99)), "unit": "ms (p99 latency)", "higher_is_better": False,
-            "n_gpus": 1, "dtype": "bf16x6", "data": "synthetic",
+            "n_gpus": 1, "dtype": st.PREC_NAMES[prec], "data": "synthetic",
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "p999_ms": float(np.percentile(lat, 99.9)), "mean_ms": float(lat.mean()),
             "requests": len(lat), "throughput_req_s": len(lat) / wall, "useful_tflops": flops / wall / 1e12,
@@ -947,7 +957,7 @@ def main():
     import paper_1301_7744_gb300 as st
     st.sttsm_set_fused_tail(args.fused_tail)
 
-    prec = st.STTSM_BF16X6 if args.prec == "bf16x6" else st.STTSM_BF16X3
+    prec = prec_code(st, args.prec)
     import synth
     Xh = synth.x_gaussian(SEED_X, P, N)
     X32 = Xh.astype(np.float32).astype(np.float64)
@@ -1003,7 +1013,7 @@ def main():
     kinds = sorted({r["kind"] for r in tc})
     kern_ms = sum(r["ms"] for r in tc)
     kern_flops = sum(r["useful_flops"] for r in tc)
-    nprod = 6 if prec == st.STTSM_BF16X6 else 3
+    nprod = 6 if args.prec.startswith("bf16x6") else 3
     pk, pk_src = peaks()
     mma_tflops = kern_flops * nprod / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else 0.0
     peak, peak_source = tensor_peak(pk, pk_src, clk, total_ms)
@@ -1021,7 +1031,7 @@ def main():
     # algorithmic bytes per level launch (mean): parent BF16 pieces read + output written
     # (pieces, or FP32 C at the last level), from the level sizes
     alg = 0.0
-    npc = 3 if prec == st.STTSM_BF16X6 else 2
+    npc = 3 if args.prec.startswith("bf16x6") else 2
     for d in range(M):
         _, _, info = st.sttsm_plan_level(M, N, P, b, prec, d)
         par = info["nodes_parent"] * info["P_parent"] * info["bm"] * npc * 2
@@ -1040,7 +1050,15 @@ def main():
                 "kernel_share_of_step": kern_ms / total_ms if total_ms > 0 else None,
                 "levels": levels}
 
-    e2e = fp64 = rel_err = cpu_base = packbw = None
+    e2e = fp64 = rel_err = cpu_base = packbw = r64 = C_r64 = None
+    if not args.no_extras and args.prec == "bf16x6":
+        # ---- the same step with the final C-block reduction in FP64 (BF16X6_R64)
+        C_r64 = torch.empty_like(C)
+        pr64 = st.STTSM_BF16X6_R64
+        tot_r, _ = time_steps(torch, lambda: st.sttsm_bcss(A, dX, M, N, P, b, C_r64, pr64, ws), 10, 3)
+        r64 = {"value": F / (tot_r / 10 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": tot_r / 10,
+               "cost_vs_bf16x6": (tot_r / 10) / ms,
+               "what": "BF16X6 products, last level's FP32 group sums added in FP64 (C-writing tiles <= 128 columns)"}
     C64 = None
     if not args.no_extras:
         # ---- BCSS pack / unpack of the same tensor (HBM-bound copies)
@@ -1052,20 +1070,22 @@ def main():
             fp64, C64 = fp64_path(st, torch, Xh, b, F, ms)
         # ---- accuracy against the oracle and the CPU baseline (rank 0; baseline at N = 1)
         if rank == 0 and not args.no_check:
-            rel_err, cpu_base = check_and_baseline(args, C, C64, Xh, X32, b, F, world)
+            rel_err, cpu_base = check_and_baseline(args, C, C64, Xh, X32, b, F, world, C_r64)
 
     # ---- the other configurations, short forms (N = 1 only): m=4 n=128 p=64, the
     # 4096-instance batch, the serving stream
     configs = None
     a_mb = A.numel() * 4 / 1e6
     if world == 1 and not args.no_extras and not args.no_configs:
-        del A, C, ws, C64
+        del A, C, ws, C64, C_r64
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         configs = {}
         for name, fn in (("m4", lambda: run_m4(args, emit=False, short=True)),
                          ("batch", lambda: run_batch(args, emit=False, short=True)),
-                         ("serve", lambda: run_serve(args, emit=False, seconds=args.configs_serve_seconds))):
+                         ("serve", lambda: run_serve(args, emit=False, seconds=args.configs_serve_seconds)),
+                         ("serve_r64", lambda: run_serve(args, emit=False, seconds=args.configs_serve_seconds,
+                                                         serve_prec="bf16x6_r64"))):
             t0 = time.perf_counter()
             configs[name] = fn()
             configs[name]["wall_seconds_of_leg"] = time.perf_counter() - t0
@@ -1091,7 +1111,7 @@ def main():
                            % a_mb, "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu_base, "e2e": e2e, "fp64_path": fp64, "rel_err": rel_err,
                 "pack_unpack": packbw,
-                "time_to_solution": tts, "configs": configs,
+                "time_to_solution": tts, "configs": configs, "final_reduction_fp64": r64,
                 "gpu_launches": args.steps * (M + (2 if "tma" in kinds else 1)), "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

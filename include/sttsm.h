@@ -64,8 +64,18 @@ typedef enum {
  *                 with FP32 accumulation in tensor memory.
  *   STTSM_BF16X3: as BF16X6 with two pieces and three products (about 2^-16
  *                 relative error per product: cheaper, less accurate).
- *   STTSM_TF32X3: reserved; returns STTSM_ERR_UNSUPPORTED. */
-typedef enum { STTSM_FP64 = 0, STTSM_BF16X6 = 1, STTSM_TF32X3 = 2, STTSM_BF16X3 = 3 } sttsm_prec;
+ *   STTSM_TF32X3: reserved; returns STTSM_ERR_UNSUPPORTED.
+ *   STTSM_BF16X6_R64, STTSM_BF16X3_R64: as BF16X6 / BF16X3, with the final
+ *                 C-block reduction in FP64 (Fig. 5's last level, C = sum over
+ *                 ibar_0 of T^(1) blocks x_0 X blocks): the FP32 partial sums
+ *                 of that level — per contraction group of <= 128 indices on
+ *                 the tensor cores, per block of b indices on the CUDA-core
+ *                 kernel of short contractions — are added in FP64 registers
+ *                 and C is rounded to FP32 once.  The last level's tiles are
+ *                 then at most 128 columns wide (more launches' worth of
+ *                 epilogue work); the other levels are unchanged. */
+typedef enum { STTSM_FP64 = 0, STTSM_BF16X6 = 1, STTSM_TF32X3 = 2, STTSM_BF16X3 = 3, STTSM_BF16X6_R64 = 4,
+               STTSM_BF16X3_R64 = 5 } sttsm_prec;
 
 /* Element types for bcss_pack / bcss_unpack. */
 typedef enum { STTSM_DTYPE_F64 = 0, STTSM_DTYPE_F32 = 1 } sttsm_dtype;

@@ -28,11 +28,14 @@ STTSM_FP64 = 0
 STTSM_BF16X6 = 1
 STTSM_TF32X3 = 2
 STTSM_BF16X3 = 3
+STTSM_BF16X6_R64 = 4
+STTSM_BF16X3_R64 = 5
 
 DTYPE_F64 = 0
 DTYPE_F32 = 1
 
-PREC_NAMES = {STTSM_FP64: "fp64", STTSM_BF16X6: "bf16x6", STTSM_TF32X3: "tf32x3", STTSM_BF16X3: "bf16x3"}
+PREC_NAMES = {STTSM_FP64: "fp64", STTSM_BF16X6: "bf16x6", STTSM_TF32X3: "tf32x3", STTSM_BF16X3: "bf16x3",
+              STTSM_BF16X6_R64: "bf16x6_r64", STTSM_BF16X3_R64: "bf16x3_r64"}
 _ERRORS = {STTSM_ERR_ARG: "invalid argument", STTSM_ERR_UNSUPPORTED: "unsupported",
            STTSM_ERR_NOMEM: "workspace too small or allocation failed", STTSM_ERR_TIMEOUT: "device wait timed out",
            STTSM_ERR_CUDA: "CUDA call failed", STTSM_ERR_BUSY: "queue full"}

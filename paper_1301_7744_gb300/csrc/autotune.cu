@@ -47,7 +47,7 @@ extern "C" int sttsm_autotune_b_measured(int m, int64_t n, int64_t p, int prec, 
     using namespace sttsm;
     if (!cands || ncand <= 0 || ncand > 64 || reps < 1 || reps > 1000) return STTSM_ERR_ARG;
     if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
-    if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
+    if (!prec_valid(prec)) return STTSM_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return STTSM_ERR_CUDA;
     const std::vector<int> cv(cands, cands + ncand);

@@ -26,7 +26,7 @@ namespace {
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int npiece(int prec) { return prec == STTSM_BF16X6 ? 3 : (prec == STTSM_BF16X3 ? 2 : 0); }
+int npiece(int prec) { return prec_npiece(prec); }
 
 // Cost model of one level launch's tiles, in SM cycles: each stage of a tile
 // costs the larger of its MMA time (products x 2 K-steps x N/2 cycles for a
@@ -52,7 +52,7 @@ double tile_cost(int nk, int ncols, int nprod, const KernelCost& k)
 
 double plan_cost(const Shape& s, int prec, int BM, int BN)
 {
-    const int nprod = prec == STTSM_BF16X3 ? 3 : 6;
+    const int nprod = prec_npiece(prec) == 2 ? 3 : 6;
     if (tc_small_mode(s)) BN = TC_SMALL_BN;
     const KernelCost k = kernel_cost(s);
     double c = 0.0;
@@ -77,6 +77,7 @@ struct Instance {
 
 struct LevelLaunch {
     int ntiles = 0;
+    int maxcols = 0;              // widest tile
     Tile* d_tiles = nullptr;
     void* d_insts = nullptr;      // TcInst[] or LevelInst[]
     std::vector<int> inst_ids;    // instance of every descriptor
@@ -215,6 +216,7 @@ int bind_workspace(sttsm_batch_plan_s* P, char* ws)
 int enqueue(sttsm_batch_plan_s* P, cudaStream_t s)
 {
     const bool fp64 = P->prec == STTSM_FP64;
+    const bool r64 = prec_r64(P->prec);
     const int np = npiece(P->prec);
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -230,10 +232,14 @@ int enqueue(sttsm_batch_plan_s* P, cudaStream_t s)
             TcInst dummy;
             memset(&dummy, 0, sizeof(dummy));
             const TcInst* ti = (const TcInst*)L.d_insts;
+            // under the R64 precisions every gathered launch sums in FP64 (its tiles are at
+            // most 128 wide) and the FP32 kernel does so at each instance's last level
             const int rc = fp64 ? launch_level_fp64(dummy.L, (const LevelInst*)L.d_insts, L.d_tiles, L.ntiles, sms, s)
-                         : (mode && small_kernel_kind() == 0) ? launch_level_small_f32_tc(ti, L.d_tiles, L.ntiles, sms, s)
+                         : (mode && (small_kernel_kind() == 0 || r64))
+                             ? launch_level_small_f32_tc(ti, L.d_tiles, L.ntiles, sms, s, r64 ? 1 : 0)
                          : mode ? launch_level_tc_small(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, s)
-                                : launch_level_tc(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, s);
+                         : r64 ? launch_level_tc_r64(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, L.maxcols, s)
+                               : launch_level_tc(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, s);
             if (rc != 0) return STTSM_ERR_CUDA;
         }
         if (w.pair.ntiles > 0 &&
@@ -270,7 +276,7 @@ int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_
 {
     if (!d || count <= 0 || !plan_out) return STTSM_ERR_ARG;
     if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
-    if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
+    if (!prec_valid(prec)) return STTSM_ERR_ARG;
     const bool fp64 = prec == STTSM_FP64;
     const int np = npiece(prec);
     const size_t esz = fp64 ? 8 : 4;
@@ -299,7 +305,8 @@ int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_
         I.buf_off[1] = off;
         off += up256((size_t)s.buf_elems[1] * esz);
         I.ws_bytes = std::max<size_t>(off, 256);
-        I.fused = !fp64 && tc_small_mode(s) && small_kernel_kind() == 0 && fused_tail_in_batches() && pair_mode(s);
+        I.fused = !fp64 && !prec_r64(prec) && tc_small_mode(s) && small_kernel_kind() == 0 && fused_tail_in_batches() &&
+                  pair_mode(s);
         I.cost = sttsm_flops(s.m, s.n, s.p, s.b);
         P->useful_flops += I.cost;
         if (ws_budget && I.ws_bytes > ws_budget) return STTSM_ERR_NOMEM;
@@ -349,9 +356,10 @@ int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_
                 if (I.fused && lv >= I.shape.m - 2) continue;   // in the pair launch
                 const int32_t e = (int32_t)L.inst_ids.size();
                 L.inst_ids.push_back(id);
-                build_level_tiles(I.shape, lv, BM, small ? TC_SMALL_BN : BN, e, tiles);
+                build_level_tiles(I.shape, lv, BM, small ? TC_SMALL_BN : (prec_r64(prec) ? R64_BN : BN), e, tiles);
             }
             L.ntiles = (int)tiles.size();
+            for (const Tile& t : tiles) L.maxcols = std::max(L.maxcols, (int)t.ncols);
             if (L.ntiles == 0) continue;
             if (cudaMalloc(&L.d_tiles, tiles.size() * sizeof(Tile)) != cudaSuccess) return STTSM_ERR_NOMEM;
             if (cudaMemcpy(L.d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess)

@@ -86,12 +86,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-int npiece_of(int prec)
-{
-    if (prec == STTSM_BF16X6) return 3;
-    if (prec == STTSM_BF16X3) return 2;
-    return 0;
-}
+int npiece_of(int prec) { return prec_npiece(prec); }
 
 // Workspace layout: [X pieces (split precisions)][A pieces (TMA-fed kernel)]
 // [temporaries buffer 0][buffer 1]; the TMA-fed kernel keeps temporaries as
@@ -310,7 +305,7 @@ int sttsm_workspace_size(int m, int64_t n, int64_t p, int b, int prec, size_t* b
 {
     if (!bytes) return STTSM_ERR_ARG;
     if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
-    if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
+    if (!prec_valid(prec)) return STTSM_ERR_ARG;
     Shape s;
     int rc = make_shape(m, n, p, b, &s);
     if (rc != STTSM_OK) return rc;
@@ -374,13 +369,15 @@ int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_
                      int32_t* G, int64_t G_cap, int64_t* ntiles_out, int64_t* nG_out, int64_t* info)
 {
     if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
-    if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
+    if (!prec_valid(prec)) return STTSM_ERR_ARG;
     Shape s;
     int rc = make_shape(m, n, p, b, &s);
     if (rc != STTSM_OK) return rc;
     if (d < 0 || d >= m) return STTSM_ERR_ARG;
     const bool fp64 = prec == STTSM_FP64;
-    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : (tc_small_mode(s) ? TC_SMALL_BN : TC_BN);
+    int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : (tc_small_mode(s) ? TC_SMALL_BN : TC_BN);
+    const bool gathered = !fp64 && !tc_small_mode(s) && !tc_tma_mode(s);
+    if (prec_r64(prec) && (d == m - 1 || gathered) && BN > R64_BN) BN = R64_BN;
     std::vector<Tile> tl;
     std::vector<int32_t> g;
     build_level_tiles(s, d, BM, BN, 0, tl);
@@ -434,7 +431,7 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
 {
     if (!A || !X || !C) return STTSM_ERR_ARG;
     if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
-    if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
+    if (!prec_valid(prec)) return STTSM_ERR_ARG;
     if (!aligned(A, 16) || !aligned(X, 16) || !aligned(C, 16)) return STTSM_ERR_ARG;
     if (n >= (int64_t)1 << 30 || p >= (int64_t)1 << 30) return STTSM_ERR_UNSUPPORTED;
     Shape s;
@@ -448,8 +445,13 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
     cudaStream_t stream = (cudaStream_t)stream_;
     const bool fp64 = prec == STTSM_FP64;
     const bool small = !fp64 && tc_small_mode(s);
-    const int BM = fp64 ? 64 : TC_BM, BN = fp64 ? 64 : (small ? TC_SMALL_BN : TC_BN);
-    const DevPlan* P = get_dev_plan(m, n, p, b, BM, BN);
+    const bool r64 = prec_r64(prec);
+    // R64: the gathered kernel sums in FP64 at every level (as in batches and serving),
+    // the TMA kernel at the last level; both then take tiles of at most 128 columns
+    const bool gathered = !fp64 && !small && !tc_tma_mode(s);
+    const int BM = fp64 ? 64 : TC_BM;
+    const int BN = fp64 ? 64 : small ? TC_SMALL_BN : (r64 && gathered) ? R64_BN : TC_BN;
+    const DevPlan* P = get_dev_plan(m, n, p, b, BM, BN, r64 && BN > R64_BN ? R64_BN : BN);
     if (!P) return STTSM_ERR_NOMEM;
     char* ws = (char*)workspace;
     void* bufs[2] = {ws + w.buf0, ws + w.buf1};
@@ -493,7 +495,10 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
             for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
             const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;
             ProfScope ps(stream, 3, d, lflops);
-            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, d < nlev - 1 ? TMA_OUT_PIECES : (d == m - 1 ? TMA_OUT_C : TMA_OUT_F32), tma_sw32(s), P->maxcols[d], stream));
+            const int out_kind = d < nlev - 1 ? TMA_OUT_PIECES
+                                 : d == m - 1 ? (r64 ? TMA_OUT_C64 : TMA_OUT_C) : TMA_OUT_F32;
+            rc = cuda_err(launch_level_tma(np, tm, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, out_kind, tma_sw32(s),
+                                           P->maxcols[d], stream));
             if (rc != STTSM_OK) return rc;
         }
         return STTSM_OK;
@@ -506,11 +511,11 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
             rc = cuda_err(launch_split_x((const float*)X, ws + w.xpieces, (int)p, (int)n, w.rows, w.Kp, np, stream));
         }
         if (rc != STTSM_OK) return rc;
-        rc = make_x_tensor_map(&ti.tmX, ws + w.xpieces, np, w.rows, w.Kp, BN);
+        rc = make_x_tensor_map(&ti.tmX, ws + w.xpieces, np, w.rows, w.Kp, small ? TC_SMALL_BN : TC_BN);
         if (rc != STTSM_OK) return rc;
     }
     // short contractions in FP32: the last two levels in one launch, T^(1) in shared memory
-    const bool pair = small && small_kernel_kind() == 0 && fused_tail_enabled() && nlev == m && P->d_pair;
+    const bool pair = small && small_kernel_kind() == 0 && fused_tail_enabled() && nlev == m && P->d_pair && !r64;
     for (int d = 0; d < nlev; ++d) {
         const LevelShape& LS = s.lv[d];
         LevelInst& L = ti.L;
@@ -541,8 +546,12 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
         }
         ProfScope ps(stream, fp64 ? 0 : 1, d, lflops);
         if (fp64) rc = cuda_err(launch_level_fp64(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
-        else if (small && small_kernel_kind() == 0) rc = cuda_err(launch_level_small_f32(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
+        // the R64 precisions: the last level sums in FP64 (the FP32 kernel for short contractions)
+        else if (small && (small_kernel_kind() == 0 || r64))
+            rc = cuda_err(launch_level_small_f32(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream, r64 && d == m - 1));
         else if (small) rc = cuda_err(launch_level_tc_small(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
+        else if (r64)
+            rc = cuda_err(launch_level_tc_r64(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, P->maxcols[d], stream));
         else rc = cuda_err(launch_level_tc(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
         if (rc != STTSM_OK) return rc;
     }

@@ -558,9 +558,68 @@ __device__ __forceinline__ void s32_compute_store(const S32Stage& S, const Level
     }
 }
 
+// The last level (k = 0) under the R64 precisions: one output row per thread,
+// columns in chunks of at most 16; the FP32 sum over each contraction block of
+// b indices is added to an FP64 sum (the cross-block accumulation of a C
+// block in FP64), and C gets the FP64 sum rounded once.
+template <int NC>
+__device__ __forceinline__ void s32_compute_store_r64(const S32Stage& S, const LevelInst& I, const Tile& t)
+{
+    constexpr int CW = NC < 16 ? NC : 16;
+    const int r = threadIdx.x;
+    const int g = t.row0 + r;
+    if (g >= I.rows_per_parent) return;
+    const int Kc = (I.Ktot + 3) & ~3;
+    const int b = I.b;
+    const int pr = g / I.R, rr = g - pr * I.R;
+    float* row = (float*)I.out + ((int64_t)t.child_base * I.P_out + pr) * I.bm + __ldg(I.OFF + I.k * I.R + rr);
+    const int64_t child_step = (int64_t)I.P_out * I.bm;
+#pragma unroll 1
+    for (int c0 = 0; c0 < NC; c0 += CW) {
+        if (c0 >= t.ncols) break;
+        uint64_t acc[CW / 2];
+        double dacc[CW];
+#pragma unroll
+        for (int e = 0; e < CW / 2; ++e) acc[e] = 0ull;
+#pragma unroll
+        for (int e = 0; e < CW; ++e) dacc[e] = 0.0;
+        int in_block = 0;
+#pragma unroll 4
+        for (int kk = 0; kk < Kc; ++kk) {
+            const uint64_t a2 = s32_dup(S.A[kk][r]);
+            const ulonglong2* xr = (const ulonglong2*)&S.X[kk][c0 + s32_xshift<NC>(kk)];
+#pragma unroll
+            for (int c4 = 0; c4 < CW / 4; ++c4) {
+                const ulonglong2 x = xr[c4];
+                s32_fma2(acc[2 * c4 + 0], a2, x.x);
+                s32_fma2(acc[2 * c4 + 1], a2, x.y);
+            }
+            if (++in_block == b || kk == Kc - 1) {
+                in_block = 0;
+#pragma unroll
+                for (int e = 0; e < CW / 2; ++e) {
+                    float lo, hi;
+                    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[e]));
+                    dacc[2 * e] += (double)lo;
+                    dacc[2 * e + 1] += (double)hi;
+                    acc[e] = 0ull;
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < CW; ++e) {
+            const int cc = t.col0 + c0 + e;
+            if (c0 + e >= t.ncols) break;
+            const int jb = cc / b, c = cc - jb * b;
+            row[(int64_t)jb * child_step + c] = (float)dacc[e];
+        }
+    }
+}
+
 template <typename Desc>
 __global__ void __launch_bounds__(S32_ROWS, S32_CTAS_PER_SM)
-level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Tile* __restrict__ tiles, int ntiles)
+level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Tile* __restrict__ tiles, int ntiles,
+                       int r64)
 {
     extern __shared__ __align__(16) unsigned char s32_raw[];
     S32Stage& S = *(S32Stage*)s32_raw;
@@ -576,7 +635,16 @@ level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Ti
         s32_commit();
         s32_wait_all();
         __syncthreads();
-        switch (s32_width_class(t.ncols)) {
+        if (r64 && I.k == 0) {
+            switch (s32_width_class(t.ncols)) {
+            case 0: s32_compute_store_r64<8>(S, I, t); break;
+            case 1: s32_compute_store_r64<16>(S, I, t); break;
+            case 2: s32_compute_store_r64<24>(S, I, t); break;
+            case 3: s32_compute_store_r64<32>(S, I, t); break;
+            case 4: s32_compute_store_r64<48>(S, I, t); break;
+            default: s32_compute_store_r64<64>(S, I, t); break;
+            }
+        } else switch (s32_width_class(t.ncols)) {
         case 0: s32_compute_store<8, 1>(S, I, t); break;
         case 1: s32_compute_store<16, 2>(S, I, t); break;
         case 2: s32_compute_store<24, 2>(S, I, t); break;
@@ -590,7 +658,7 @@ level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Ti
 
 template <typename Desc>
 static int launch_small_f32(const Desc* d_insts, const LevelInst& inst0, const Tile* d_tiles, int ntiles, int num_sms,
-                            cudaStream_t s)
+                            cudaStream_t s, int r64)
 {
     if (ntiles <= 0) return 0;
     static std::mutex mu;
@@ -607,21 +675,22 @@ static int launch_small_f32(const Desc* d_insts, const LevelInst& inst0, const T
         }
     }
     const int grid = ntiles < num_sms * S32_CTAS_PER_SM ? ntiles : num_sms * S32_CTAS_PER_SM;
-    level_small_f32_kernel<Desc><<<grid, S32_ROWS, S32_SMEM, s>>>(d_insts, inst0, d_tiles, ntiles);
+    level_small_f32_kernel<Desc><<<grid, S32_ROWS, S32_SMEM, s>>>(d_insts, inst0, d_tiles, ntiles, r64);
     return (int)cudaGetLastError();
 }
 
 int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
-                           int num_sms, cudaStream_t s)
+                           int num_sms, cudaStream_t s, int r64)
 {
-    return launch_small_f32<LevelInst>(d_insts, inst0, d_tiles, ntiles, num_sms, s);
+    return launch_small_f32<LevelInst>(d_insts, inst0, d_tiles, ntiles, num_sms, s, r64);
 }
 
-int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s)
+int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s,
+                              int r64)
 {
     LevelInst none;
     memset(&none, 0, sizeof(none));
-    return launch_small_f32<TcInst>(d_insts, none, d_tiles, ntiles, num_sms, s);
+    return launch_small_f32<TcInst>(d_insts, none, d_tiles, ntiles, num_sms, s, r64);
 }
 
 // ------------------------------------------------------------------ FP64 level kernel

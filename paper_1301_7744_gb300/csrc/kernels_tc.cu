@@ -42,6 +42,7 @@
 #include <cuda_bf16.h>
 #include <cuda.h>
 #include <mutex>
+#include <type_traits>
 #include "common.cuh"
 #include "launch.h"
 #include "tc_ptx.cuh"
@@ -139,8 +140,8 @@ __device__ __forceinline__ GatherRow gather_row(const Tile& t, const LevelInst& 
 
 // Scatter n (<= N) values of one output row into the children's blocks:
 // column c0 + e goes to child (c0 + e) / b, entry (rr, (c0 + e) % b).
-template <int N>
-__device__ __forceinline__ void store_row(const Tile& t, const LevelInst& I, int row, int colbase, const float* vals)
+template <int N, typename V>
+__device__ __forceinline__ void store_row(const Tile& t, const LevelInst& I, int row, int colbase, const V* vals)
 {
     const int g = t.row0 + row;
     if (g >= I.rows_per_parent) return;
@@ -154,12 +155,14 @@ __device__ __forceinline__ void store_row(const Tile& t, const LevelInst& I, int
     const int64_t node_stride = I.P_out * I.bm;
 #pragma unroll
     for (int e = 0; e < N; ++e) {
-        if (e < nvalid) dst[(int64_t)bk * c] = vals[e];
+        if (e < nvalid) dst[(int64_t)bk * c] = (float)vals[e];
         if (++c == b) { c = 0; dst += node_stride; }
     }
 }
 
-template <int NP>
+// R64: the workers' register sums are FP64 over 32 columns each (the C-block
+// reduction of the R64 precisions), so tiles are at most 128 columns wide.
+template <int NP, bool R64>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__ insts,
                 const Tile* __restrict__ tiles, int ntiles, int* status)
@@ -209,7 +212,9 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
         const int quad = warp & 3, cq = warp >> 2;
         const int row = quad * 32 + lane;                 // tile row and TMEM lane
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-        const int colbase = cq * 64;                      // epilogue columns
+        constexpr int AW = R64 ? 32 : 64;                 // accumulator columns per thread
+        using AccT = typename std::conditional<R64, double, float>::type;
+        const int colbase = cq * AW;                      // epilogue columns
         const bool tma_thread = threadIdx.x == 0;
         int stage = 0;
         uint32_t phase = 0;
@@ -217,7 +222,7 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
         int last_stage_issued = -1;
         uint32_t last_phase_issued = 0;
         bool ok = true;
-        float acc[64];
+        AccT acc[AW];
         float vn[8];
         bool prefetched = false;
 
@@ -228,11 +233,11 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
             tc_fence_after();
             if (active) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < AW / 8; ++c) {
                     float v[8];
                     tmem_ld_32x32b_x8(tmem_d0 + lane_off + colbase + c * 8, v);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
+                    for (int i = 0; i < 8; ++i) acc[c * 8 + i] += (AccT)v[i];
                 }
             }
             tc_fence_before();
@@ -250,7 +255,7 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
             const int nk = (I.Ktot + TC_KC - 1) / TC_KC;
             const bool active = colbase < t.ncols;        // warp-uniform
 #pragma unroll
-            for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+            for (int i = 0; i < AW; ++i) acc[i] = 0;
             if (!prefetched) gather8(GR, I, cq * 8, vn);  // stage 0 of the tile
             prefetched = false;
             for (int ks = 0; ks < nk; ++ks) {
@@ -303,18 +308,18 @@ level_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst* __restrict__
             // every MMA of the tile has completed (last d0_full commit): add D1
             if (active) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < AW / 8; ++c) {
                     float v[8];
                     tmem_ld_32x32b_x8(tmem_d1 + lane_off + colbase + c * 8, v);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
+                    for (int i = 0; i < 8; ++i) acc[c * 8 + i] += (AccT)v[i];
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(d1_empty);
             // scatter the row's 64 columns into the children's blocks
-            if (active && valid) store_row<64>(t, I, row, colbase, acc);
+            if (active && valid) store_row<AW>(t, I, row, colbase, acc);
         }
         // make sure no TMA write is still in flight before the CTA exits
         if (tma_thread && !ok && last_stage_issued >= 0) {
@@ -693,35 +698,47 @@ int launch_level_tc_small(int npiece, const TcInst& inst0, const TcInst* d_insts
     return (int)cudaGetLastError();
 }
 
+template <int NP, bool R64>
+static int launch_tc_variant(const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles, int grid,
+                             int* d_status, cudaStream_t s)
+{
+    // the shared-memory opt-in is set once per device (never inside a stream capture after the first call)
+    static std::mutex mu;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            const cudaError_t e = cudaFuncSetAttribute(level_tc_kernel<NP, R64>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<NP>::BYTES);
+            if (e != cudaSuccess) return (int)e;
+            attr_set[dev] = true;
+        }
+    }
+    level_tc_kernel<NP, R64><<<grid, NUM_THREADS, Smem<NP>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
+    return (int)cudaGetLastError();
+}
+
 int launch_level_tc(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
                     int num_sms, int* d_status, cudaStream_t s)
 {
     if (ntiles <= 0) return 0;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
-    // the shared-memory opt-in is set once per device (never inside a stream capture after the first call)
-    static std::mutex mu;
-    static bool attr_set[2][64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (dev >= 0 && dev < 64 && !attr_set[npiece - 2][dev]) {
-            cudaError_t e = npiece == 3
-                ? cudaFuncSetAttribute(level_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<3>::BYTES)
-                : cudaFuncSetAttribute(level_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<2>::BYTES);
-            if (e != cudaSuccess) return (int)e;
-            attr_set[npiece - 2][dev] = true;
-        }
-    }
-    if (npiece == 3) {
-        level_tc_kernel<3><<<grid, NUM_THREADS, Smem<3>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
-    } else if (npiece == 2) {
-        level_tc_kernel<2><<<grid, NUM_THREADS, Smem<2>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status);
-    } else {
-        return (int)cudaErrorInvalidValue;
-    }
-    return (int)cudaGetLastError();
+    if (npiece == 3) return launch_tc_variant<3, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    if (npiece == 2) return launch_tc_variant<2, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    return (int)cudaErrorInvalidValue;
+}
+
+int launch_level_tc_r64(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
+                        int num_sms, int* d_status, int max_cols, cudaStream_t s)
+{
+    if (ntiles <= 0) return 0;
+    if (max_cols > 128) return (int)cudaErrorInvalidValue;   // 32 FP64 columns per worker
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    if (npiece == 3) return launch_tc_variant<3, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    if (npiece == 2) return launch_tc_variant<2, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, s);
+    return (int)cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ bounded-wait probe

@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 #include <cuda.h>
 #include <mutex>
+#include <type_traits>
 #include "common.cuh"
 #include "launch.h"
 #include "tc_ptx.cuh"
@@ -95,6 +96,19 @@ __device__ __forceinline__ void tmem_fold_n(float* acc, uint32_t taddr, int n)
         tmem_ld_32x32b_x8(taddr + c * 8, v);
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc[c * 8 + i] += v[i];
+    }
+}
+
+// acc[0..31] += 32 consecutive TMEM columns, accumulated in FP64 (the C-block
+// reduction of the R64 precisions)
+__device__ __forceinline__ void tmem_fold32_f64(double* acc, uint32_t taddr)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float v[8];
+        tmem_ld_32x32b_x8(taddr + c * 8, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[c * 8 + i] += (double)v[i];
     }
 }
 
@@ -347,7 +361,12 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
         uint32_t group_phase = 0;
         bool ok = true;
-        float acc[64];
+        // FP32 register sums, or FP64 ones for C under the R64 precisions (32 columns
+        // per thread: tiles of at most 128 columns)
+        constexpr bool R64 = OUT == TMA_OUT_C64;
+        constexpr int AW = R64 ? 32 : 64;
+        using AccT = typename std::conditional<R64, double, float>::type;
+        AccT acc[AW];
         for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
             const Tile t = tiles[ti];
             const TmaInst& TI = insts ? insts[t.inst] : inst0;
@@ -356,22 +375,30 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             const int ngroups = d0_groups(nk);
             // (the FP32 writer of C keeps whole 64-column quarters: its rows are
             // contiguous, and longer runs per thread store faster)
-            const int cw = OUT == TMA_OUT_C ? 64 : ((((t.ncols + 15) & ~15) + 3) / 4 + 7) & ~7;
+            const int cw = R64 ? 32 : OUT == TMA_OUT_C ? 64 : ((((t.ncols + 15) & ~15) + 3) / 4 + 7) & ~7;
             const int colbase = cq * cw;
             const bool active = colbase < t.ncols;
 #pragma unroll
-            for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+            for (int i = 0; i < AW; ++i) acc[i] = 0;
             for (int gi = 0; gi < ngroups; ++gi) {
                 if (!mbar_wait(d0_full, group_phase, abort_flag, status)) { ok = false; break; }
                 group_phase ^= 1u;
                 tc_fence_after();
-                if (active) { if (cw == 64) tmem_fold64(acc, tmem_d0 + lane_off + (uint32_t)colbase); else tmem_fold_n(acc, tmem_d0 + lane_off + (uint32_t)colbase, cw); }
+                if (active) {
+                    if constexpr (R64) tmem_fold32_f64(acc, tmem_d0 + lane_off + (uint32_t)colbase);
+                    else if (cw == 64) tmem_fold64(acc, tmem_d0 + lane_off + (uint32_t)colbase);
+                    else tmem_fold_n(acc, tmem_d0 + lane_off + (uint32_t)colbase, cw);
+                }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(d0_empty);
             }
             if (!ok) break;
-            if (active) { if (cw == 64) tmem_fold64(acc, tmem_d1 + lane_off + (uint32_t)colbase); else tmem_fold_n(acc, tmem_d1 + lane_off + (uint32_t)colbase, cw); }
+            if (active) {
+                if constexpr (R64) tmem_fold32_f64(acc, tmem_d1 + lane_off + (uint32_t)colbase);
+                else if (cw == 64) tmem_fold64(acc, tmem_d1 + lane_off + (uint32_t)colbase);
+                else tmem_fold_n(acc, tmem_d1 + lane_off + (uint32_t)colbase, cw);
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(d1_empty);
@@ -393,7 +420,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                         dst[(int64_t)bk * c] = acc[e];
                         if (++c == b) { c = 0; dst += I.P_out * I.bm; }
                     }
-                } else if constexpr (OUT == TMA_OUT_C) {
+                } else if constexpr (OUT == TMA_OUT_C || OUT == TMA_OUT_C64) {
                     float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
                     // the FP32 output is C (k = 0): a row's columns are contiguous within a
                     // child's block, and b (16 or a multiple of 32) keeps groups of 4 inside blocks
@@ -402,20 +429,22 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                         // multiples of 8 floats, and b (a multiple of 16) keeps groups of 8
                         // inside blocks
 #pragma unroll
-                        for (int e = 0; e < 64; e += 8) {
+                        for (int e = 0; e < AW; e += 8) {
                             if (e >= nvalid) break;
                             asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-                                         :: "l"(dst + c), "f"(acc[e]), "f"(acc[e + 1]), "f"(acc[e + 2]), "f"(acc[e + 3]),
-                                            "f"(acc[e + 4]), "f"(acc[e + 5]), "f"(acc[e + 6]), "f"(acc[e + 7])
+                                         :: "l"(dst + c), "f"((float)acc[e]), "f"((float)acc[e + 1]), "f"((float)acc[e + 2]),
+                                            "f"((float)acc[e + 3]), "f"((float)acc[e + 4]), "f"((float)acc[e + 5]),
+                                            "f"((float)acc[e + 6]), "f"((float)acc[e + 7])
                                          : "memory");
                             c += 8;
                             if (c == b) { c = 0; dst += I.P_out * I.bm; }
                         }
                     } else {
 #pragma unroll
-                        for (int e = 0; e < 64; e += 4) {
+                        for (int e = 0; e < AW; e += 4) {
                             if (e >= nvalid) break;
-                            *(float4*)(dst + c) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                            *(float4*)(dst + c) = make_float4((float)acc[e], (float)acc[e + 1], (float)acc[e + 2],
+                                                              (float)acc[e + 3]);
                             c += 4;
                             if (c == b) { c = 0; dst += I.P_out * I.bm; }
                         }
@@ -567,18 +596,21 @@ int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, c
     const int narrow = max_cols <= 64 ? 1 : 0;
     if (ntiles <= 0) return 0;
     if (npiece != 2 && npiece != 3) return (int)cudaErrorInvalidValue;
-    if (out_kind < TMA_OUT_PIECES || out_kind > TMA_OUT_F32) return (int)cudaErrorInvalidValue;
+    if (out_kind < TMA_OUT_PIECES || out_kind > TMA_OUT_C64) return (int)cudaErrorInvalidValue;
+    if (out_kind == TMA_OUT_C64 && max_cols > 128) return (int)cudaErrorInvalidValue;   // 32 FP64 columns per thread
     const int grid = ntiles < num_sms ? ntiles : num_sms;
     if (npiece == 2) {
         switch (out_kind) {
         case TMA_OUT_PIECES: return launch_tma_b<2, TMA_OUT_PIECES>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
         case TMA_OUT_C: return launch_tma_b<2, TMA_OUT_C>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+        case TMA_OUT_C64: return launch_tma_b<2, TMA_OUT_C64>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
         default: return launch_tma_b<2, TMA_OUT_F32>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
         }
     }
     switch (out_kind) {
     case TMA_OUT_PIECES: return launch_tma_b<3, TMA_OUT_PIECES>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
     case TMA_OUT_C: return launch_tma_b<3, TMA_OUT_C>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+    case TMA_OUT_C64: return launch_tma_b<3, TMA_OUT_C64>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
     default: return launch_tma_b<3, TMA_OUT_F32>(sw32, inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
     }
 }

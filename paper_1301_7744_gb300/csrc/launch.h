@@ -37,12 +37,19 @@ constexpr int TC_BN = 256;
 constexpr int TC_KC = 32;
 int launch_level_tc(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
                     int num_sms, int* d_status, cudaStream_t s);
+// The same with the register sums in FP64 (the R64 precisions); every tile at
+// most 128 columns (max_cols: the widest).
+int launch_level_tc_r64(int npiece, const TcInst& inst0, const TcInst* d_insts, const Tile* d_tiles, int ntiles,
+                        int num_sms, int* d_status, int max_cols, cudaStream_t s);
 
 // FP32 CUDA-core kernel for short contractions (n̄ b <= 64): tiles of 128 rows
 // x <= 64 columns, X read from the instance's FP32 X (LevelInst::X).
+// r64: instances at their last level (k = 0) add the FP32 sums of their
+// contraction blocks in FP64 (the R64 precisions).
 int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
-                           int num_sms, cudaStream_t s);
-int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s);
+                           int num_sms, cudaStream_t s, int r64 = 0);
+int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s,
+                              int r64 = 0);
 
 // Levels m-2 and m-1 of short contractions fused (kernels_pair.cu): the
 // descriptor describes level m-2 with out = C; tiles from build_pair_tiles.
@@ -79,7 +86,9 @@ struct TmaInst {
 // sw32: every instance of the launch has b an odd multiple of 16 (one box per
 // 16-wide K slice, 32-byte swizzle); otherwise every instance has b a multiple
 // of 32 (one box per 32-wide stage).
-constexpr int TMA_OUT_PIECES = 0, TMA_OUT_C = 1, TMA_OUT_F32 = 2;
+// TMA_OUT_C64 writes C like TMA_OUT_C with the register sums in FP64 (the R64
+// precisions; tiles of at most 128 columns).
+constexpr int TMA_OUT_PIECES = 0, TMA_OUT_C = 1, TMA_OUT_F32 = 2, TMA_OUT_C64 = 3;
 
 // A wait that never completes, bounded by limit_ns; raises *d_status on timeout.
 int launch_wait_probe(int* d_status, unsigned long long limit_ns, cudaStream_t s);

@@ -100,6 +100,7 @@ extern "C" int sttsm_bcss_noalloc(const void* A, const void* X, int m, int64_t n
 {
     if (!A || !X || !C) return STTSM_ERR_ARG;
     if (prec == STTSM_TF32X3) return STTSM_ERR_UNSUPPORTED;
+    if (prec_r64(prec)) return STTSM_ERR_UNSUPPORTED;
     if (prec != STTSM_FP64 && prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_ARG;
     if (((uintptr_t)A | (uintptr_t)X | (uintptr_t)C) % 16 != 0) return STTSM_ERR_ARG;
     if (n >= (int64_t)1 << 30 || p >= (int64_t)1 << 30) return STTSM_ERR_UNSUPPORTED;

@@ -183,7 +183,7 @@ void build_pair_tiles(const Shape& s, int32_t inst, std::vector<Tile>& tiles)
 
 namespace {
 std::mutex g_mu;
-std::map<std::tuple<int, int, int64_t, int64_t, int, int, int>, DevPlan*> g_plans;
+std::map<std::tuple<int, int, int64_t, int64_t, int, int, int, int>, DevPlan*> g_plans;
 
 void free_plan(DevPlan* P)
 {
@@ -196,11 +196,12 @@ void free_plan(DevPlan* P)
 }
 }  // namespace
 
-const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN)
+const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN, int bn_last)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    auto key = std::make_tuple(dev, m, n, p, b, BM, BN);
+    if (bn_last <= 0) bn_last = BN;
+    auto key = std::make_tuple(dev, m, n, p, b, BM, BN, bn_last);
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) return it->second;
@@ -214,7 +215,7 @@ const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN)
     for (int d = 0; d < m; ++d) {
         std::vector<Tile> tiles;
         std::vector<int32_t> G;
-        build_level_tiles(P->shape, d, BM, BN, 0, tiles);
+        build_level_tiles(P->shape, d, BM, d == m - 1 ? bn_last : BN, 0, tiles);
         build_level_G(P->shape, d, G);
         P->ntiles[d] = (int)tiles.size();
         for (const Tile& t : tiles) P->maxcols[d] = std::max(P->maxcols[d], (int)t.ncols);

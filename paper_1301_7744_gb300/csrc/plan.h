@@ -6,8 +6,20 @@
 #include <stdint.h>
 #include <vector>
 #include "common.cuh"
+#include "sttsm.h"
 
 namespace sttsm {
+
+// BF16 pieces of a precision (0 for FP64), whether its last level sums in
+// FP64 (the R64 precisions), and whether the library accepts it.
+inline int prec_npiece(int prec)
+{
+    return (prec == STTSM_BF16X6 || prec == STTSM_BF16X6_R64) ? 3 : (prec == STTSM_BF16X3 || prec == STTSM_BF16X3_R64) ? 2 : 0;
+}
+inline bool prec_r64(int prec) { return prec == STTSM_BF16X6_R64 || prec == STTSM_BF16X3_R64; }
+inline bool prec_valid(int prec) { return prec == STTSM_FP64 || prec_npiece(prec) > 0; }
+// Widest tile of the last level under the R64 precisions (32 FP64 sums per epilogue thread).
+constexpr int R64_BN = 128;
 
 struct LevelShape {
     int d, k;                  // level d writes T^(k), k = m-1-d
@@ -81,7 +93,8 @@ struct DevPlan {
 
 // Cached device plan for (shape, tile sizes) on the current device; nullptr
 // on allocation failure.  Thread-safe.  The first call for a shape allocates
-// and copies synchronously (do it before any stream capture).
-const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN);
+// and copies synchronously (do it before any stream capture).  bn_last (0 =
+// BN): tile width bound of the last level.
+const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN, int bn_last = 0);
 
 }  // namespace sttsm

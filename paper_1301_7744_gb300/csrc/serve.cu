@@ -150,6 +150,7 @@ struct Staging {
 
 struct sttsm_serve_s {
     int prec = 0, np = 0, device = 0, sms = 148;
+    bool r64 = false;                    // the last level sums in FP64 (R64 precisions)
     size_t queue_cap = 0;
     char* arena_base = nullptr;
     Arena* arena = nullptr;
@@ -261,7 +262,10 @@ int admit(sttsm_serve_s* H, Req& R, const TableSet& T)
     R.inst.assign(s.m, TcInst());
     if (R.tma) R.tinst.assign(s.m, TmaInst());
     for (int d = 0; d < s.m; ++d) {
-        build_level_tiles(s, d, TC_BM, box, 0, R.tiles[d]);
+        // R64: the gathered kernel sums in FP64 at every level and the TMA kernel at
+        // the last one, with tiles of at most 128 columns there
+        const int bn = (H->r64 && !R.small && (!R.tma || d == s.m - 1)) ? R64_BN : box;
+        build_level_tiles(s, d, TC_BM, bn, 0, R.tiles[d]);
         const int32_t* G = (const int32_t*)(H->table_base + T.off + T.level_off[d]);
         const LevelShape& LS = s.lv[d];
         TcInst& T = R.inst[d];
@@ -389,15 +393,19 @@ int launch_step(sttsm_serve_s* H)
         const Tile* dt = (const Tile*)(S.d + o_t[k]);
         const int n = (int)tiles[k].size();
         int lrc;
-        if (k == 0) lrc = launch_level_tc(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, H->stream);
-        else if (k == 1 && small_kernel_kind() == 0) lrc = launch_level_small_f32_tc((const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->stream);
+        int maxc = 0;
+        for (const Tile& t : tiles[k]) maxc = std::max(maxc, (int)t.ncols);
+        if (k == 0 && H->r64)
+            lrc = launch_level_tc_r64(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, maxc, H->stream);
+        else if (k == 0) lrc = launch_level_tc(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, H->stream);
+        else if (k == 1 && (small_kernel_kind() == 0 || H->r64))
+            lrc = launch_level_small_f32_tc((const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->stream, H->r64 ? 1 : 0);
         else if (k == 1) lrc = launch_level_tc_small(H->np, dummy, (const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->status, H->stream);
         else if (k == 6) lrc = launch_level_pair_f32_tc((const TcInst*)(S.d + o_i[2]), dt, n, H->sms, H->stream);
         else {
-            int maxc = 0;
-            for (const Tile& t : tiles[k]) maxc = std::max(maxc, (int)t.ncols);
+            const int ck = H->r64 ? TMA_OUT_C64 : TMA_OUT_C;
             lrc = launch_level_tma(H->np, tdummy, (const TmaInst*)(S.d + o_ti[k - 2]), dt, n, H->sms, H->status,
-                                   (k & 1) == 1 ? TMA_OUT_C : TMA_OUT_PIECES, k >= 4, maxc, H->stream);
+                                   (k & 1) == 1 ? ck : TMA_OUT_PIECES, k >= 4, maxc, H->stream);
         }
         if (lrc != 0) return STTSM_ERR_CUDA;
     }
@@ -526,10 +534,11 @@ extern "C" {
 int sttsm_serve_create(size_t hbm_budget_bytes, int prec, int queue_cap, void** handle)
 {
     if (!handle || hbm_budget_bytes < 256 || queue_cap < 1) return STTSM_ERR_ARG;
-    if (prec != STTSM_BF16X6 && prec != STTSM_BF16X3) return STTSM_ERR_UNSUPPORTED;
+    if (prec_npiece(prec) == 0) return STTSM_ERR_UNSUPPORTED;
     sttsm_serve_s* H = new sttsm_serve_s();
     H->prec = prec;
-    H->np = prec == STTSM_BF16X6 ? 3 : 2;
+    H->np = prec_npiece(prec);
+    H->r64 = prec_r64(prec);
     H->queue_cap = (size_t)queue_cap;
     cudaGetDevice(&H->device);
     if (cudaDeviceGetAttribute(&H->sms, cudaDevAttrMultiProcessorCount, H->device) != cudaSuccess || H->sms <= 0) H->sms = 148;
@@ -573,7 +582,7 @@ int sttsm_serve_submit(void* h, const sttsm_desc* d, uint64_t* ticket)
     if (rc != STTSM_OK) return rc;
     R.small = tc_small_mode(R.s);
     R.tma = tc_tma_mode(R.s);
-    R.fused = R.small && small_kernel_kind() == 0 && fused_tail_in_batches() && pair_mode(R.s);
+    R.fused = R.small && !H->r64 && small_kernel_kind() == 0 && fused_tail_in_batches() && pair_mode(R.s);
     R.rows = (int)(R.s.pbar * R.s.b);
     R.Kp = (int)(((R.s.nbar * R.s.b) + 7) / 8 * 8);
     R.x_off = 0;

@@ -41,17 +41,19 @@ def make_batch(st, count, seed, fp64, cands=(4, 8, 16), small=True):
     return prec, insts, host
 
 
-@pytest.mark.parametrize("fp64,kind", [(False, 0), (False, 1), (True, 0)])
-def test_batch_equals_single_instance_runs(st, fp64, kind):
+@pytest.mark.parametrize("fp64,kind,r64", [(False, 0, False), (False, 1, False), (True, 0, False), (False, 0, True)])
+def test_batch_equals_single_instance_runs(st, fp64, kind, r64):
     st.sttsm_set_small_kernel(kind)
     try:
-        _batch_equals_single(st, fp64)
+        _batch_equals_single(st, fp64, r64)
     finally:
         st.sttsm_set_small_kernel(0)
 
 
-def _batch_equals_single(st, fp64):
+def _batch_equals_single(st, fp64, r64=False):
     prec, insts, host = make_batch(st, 48, 3, fp64)
+    if r64:
+        prec = st.STTSM_BF16X6_R64
     plan = st.BatchPlan(insts, prec)
     ws = torch.empty(max(plan.workspace_size(), 1), dtype=torch.uint8, device="cuda")
     plan.run(ws)

@@ -171,12 +171,12 @@ def test_measured_autotune_rejects_bad_arguments_on_the_host(st):
 @pytest.mark.parametrize("m,n,p,b", [(3, 24, 24, 8), (3, 768, 768, 64), (3, 768, 768, 32), (3, 768, 768, 48),
                                      (4, 128, 64, 8), (4, 128, 64, 16), (4, 128, 64, 32), (5, 37, 20, 4),
                                      (2, 9, 11, 3), (1, 10, 7, 4), (6, 20, 12, 8), (3, 320, 320, 32)])
-@pytest.mark.parametrize("precname", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("precname", ["fp64", "bf16x6", "bf16x6_r64"])
 def test_work_list_issues_the_table4_count(st, m, n, p, b, precname):
     """The multiply-adds the emitted tiles cover (valid rows x columns x n̄ b, times
     2), summed over every tile of every level, equal the oracle's loop-counted
     Tbl. 4 flop count exactly: the work list neither drops nor repeats work."""
-    prec = st.STTSM_FP64 if precname == "fp64" else st.STTSM_BF16X6
+    prec = {"fp64": st.STTSM_FP64, "bf16x6": st.STTSM_BF16X6, "bf16x6_r64": st.STTSM_BF16X6_R64}[precname]
     nbar = -(-n // b)
     total = 0
     for d in range(m):

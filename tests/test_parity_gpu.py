@@ -30,7 +30,8 @@ def st():
 
 
 def prec_of(st, name):
-    return {"fp64": st.STTSM_FP64, "bf16x6": st.STTSM_BF16X6, "bf16x3": st.STTSM_BF16X3}[name]
+    return {"fp64": st.STTSM_FP64, "bf16x6": st.STTSM_BF16X6, "bf16x3": st.STTSM_BF16X3,
+            "bf16x6_r64": st.STTSM_BF16X6_R64, "bf16x3_r64": st.STTSM_BF16X3_R64}[name]
 
 
 def dtype_of(name):
@@ -451,3 +452,27 @@ def test_fused_last_two_levels(st, m, n, p, b):
     assert np.array_equal(fused, two)
     ref = oracle_C_bcss(A, X, m, p, b)
     assert rel_fro(fused, ref) <= TOL["bf16x6"] and rel_max(fused, ref) <= TOL["bf16x6"]
+
+
+# The R64 precisions: the last level's FP32 partial sums added in FP64.  Shapes
+# on every kernel path: TMA (b = 32, 16, 48), the gathered kernel (b = 8, 24),
+# the FP32 kernel of short contractions, and parents wider than 128 columns.
+R64_SHAPES = [(3, 96, 96, 32), (3, 100, 90, 16), (3, 150, 100, 48), (4, 70, 40, 16), (3, 70, 60, 8),
+              (3, 130, 100, 24), (4, 20, 12, 5), (5, 16, 16, 8), (3, 320, 320, 32)]
+
+
+@pytest.mark.parametrize("m,n,p,b", R64_SHAPES)
+@pytest.mark.parametrize("precname", ["bf16x6_r64", "bf16x3_r64"])
+def test_r64_final_reduction(st, m, n, p, b, precname):
+    A, X = inputs(m, n, p, seed_a=m + 2 * n, seed_x=p + 3, fp32=True)
+    Ab = device_bcss_from_dense(st, A, m, n, b, torch.float32)
+    got = run_sttsm(st, Ab, X, m, n, p, b, prec_of(st, precname))
+    base = run_sttsm(st, Ab, X, m, n, p, b, prec_of(st, precname[:-4]))
+    ref = oracle_C_bcss(A, X, m, p, b)
+    tol = 1e-6 if precname.startswith("bf16x6") else 1e-4
+    e_r64, e_base = rel_fro(got, ref), rel_fro(base, ref)
+    print("%s m=%d n=%d p=%d b=%d: rel err %.3e (%.3e without), elementwise %.3e"
+          % (precname, m, n, p, b, e_r64, e_base, rel_max(got, ref)))
+    assert not np.isnan(got).any()
+    assert e_r64 <= tol and rel_max(got, ref) <= tol
+    assert rel_fro(got, base) <= tol

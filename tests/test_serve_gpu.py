@@ -227,3 +227,25 @@ def test_fused_tail_in_serving_equals_two_launches(st):
             st.sttsm_set_fused_tail(st.FUSED_TAIL_CALLS)
     for a, b in zip(*outs):
         assert not np.isnan(a).any() and np.array_equal(a, b)
+
+
+def test_r64_serving_equals_alone_and_oracle(st):
+    """A server in BF16X6_R64 (the final C-block reduction in FP64): requests on the TMA
+    kernel (b = 16, 32), the gathered kernel (b = 8) and the FP32 short kernel give the
+    same bits as the same request alone in BF16X6_R64, and the oracle's C."""
+    shapes = [(3, 100, 90, 16), (3, 96, 96, 32), (3, 70, 60, 8), (5, 16, 16, 4), (4, 40, 30, 8)]
+    reqs = [make_request(st, 7500 + i, m, n, p, b) for i, (m, n, p, b) in enumerate(shapes)]
+    torch.cuda.synchronize()
+    prec = st.STTSM_BF16X6_R64
+    srv = st.Server(4 << 30, prec)
+    tickets = [srv.submit(r["Ab"], r["dX"], r["C"], r["m"], r["n"], r["p"], r["b"]) for r in reqs]
+    wait_all(srv, tickets)
+    srv.destroy()
+    for r in reqs:
+        got = r["C"].double().cpu().numpy()
+        C = torch.empty_like(r["C"])
+        st.sttsm_bcss(r["Ab"], r["dX"], r["m"], r["n"], r["p"], r["b"], C, prec,
+                      st.workspace_tensor(r["m"], r["n"], r["p"], r["b"], prec))
+        torch.cuda.synchronize()
+        assert np.array_equal(got, C.double().cpu().numpy()), (r["m"], r["n"], r["b"])
+        assert rel_fro(got, oracle_C_bcss(r["A"], r["X"], r["m"], r["p"], r["b"])) <= 1e-6
