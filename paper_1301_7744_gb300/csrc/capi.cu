@@ -146,7 +146,8 @@ bool fused_tail_in_batches() { return g_fused_tail.load() == 2; }
 int* batch_status_word() { return status_dev(); }
 int peek_status_word() { return g_status_host ? __atomic_load_n(g_status_host, __ATOMIC_SEQ_CST) : 0; }
 
-int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, int npiece, int b, int m, int k)
+int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, int npiece, int b, int m, int k,
+                       bool order16x8)
 {
     auto enc = get_encode_fn();
     if (!enc) return STTSM_ERR_CUDA;
@@ -154,6 +155,35 @@ int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, i
     for (int a = 0; a < m - 1; ++a) R *= b;
     const int64_t bm = R * b;
     int64_t bq = 1;
+    if (order16x8) {
+        // tiles of 16 fastest x 8 next rows (m = 3, 4): one 5-D box per 16-wide slice,
+        // dims {contraction a, f, r1, r2, block x piece} for q = 0 and {f, a, r1, r2, ...}
+        // for q >= 1, where the row modes f, r1, r2 sit at stored position t (t < q) or
+        // t + 1 and the contraction at position q
+        auto bpow = [&](int e) { int64_t v = 1; for (int i = 0; i < e; ++i) v *= b; return v; };
+        for (int q = 0; q <= k; ++q) {
+            auto pos = [&](int t) { return t < q ? t : t + 1; };
+            const cuuint64_t r2ext = m == 4 ? (cuuint64_t)b : 1;
+            const cuuint64_t r2str = (cuuint64_t)(m == 4 ? bpow(pos(2)) : bm) * 2;
+            cuuint64_t dims[5] = {(cuuint64_t)b, (cuuint64_t)b, (cuuint64_t)b, r2ext, (cuuint64_t)(nblocks * npiece)};
+            cuuint64_t strides[4];
+            if (q == 0) {
+                strides[0] = (cuuint64_t)bpow(pos(0)) * 2;   // f
+            } else {
+                strides[0] = (cuuint64_t)bpow(q) * 2;        // contraction
+            }
+            strides[1] = (cuuint64_t)bpow(pos(1)) * 2;       // r1
+            strides[2] = r2str;                               // r2
+            strides[3] = (cuuint64_t)bm * 2;                  // block x piece
+            cuuint32_t box[5] = {16, 16, 8, 1, (cuuint32_t)npiece};
+            cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+            const CUresult r = enc(&maps[q], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(pieces), dims, strides,
+                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return STTSM_ERR_CUDA;
+        }
+        return STTSM_OK;
+    }
     if (tma_sw32_b(b)) {
         // one box per 16-wide K slice, 32-byte swizzle
         for (int q = 0; q <= k; ++q, bq *= b) {
@@ -380,7 +410,7 @@ int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_
     if (prec_r64(prec) && (d == m - 1 || gathered) && BN > R64_BN) BN = R64_BN;
     std::vector<Tile> tl;
     std::vector<int32_t> g;
-    build_level_tiles(s, d, BM, BN, 0, tl);
+    build_level_tiles(s, d, BM, BN, 0, tl, !fp64 && tma_order16x8(s, d));
     build_level_G(s, d, g);
     if (ntiles_out) *ntiles_out = (int64_t)tl.size();
     if (nG_out) *nG_out = (int64_t)g.size();
@@ -474,7 +504,8 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
         for (int d = 0; d < nlev; ++d) {
             const LevelShape& LS = s.lv[d];
             const void* parent = d == 0 ? (const void*)(ws + w.apieces) : bufs[(d - 1) & 1];
-            rc = make_a_tensor_maps(tm.tmA, parent, LS.nodes_parent * LS.P_parent, np, b, m, LS.k);
+            const bool o16 = tma_order16x8(s, d);
+            rc = make_a_tensor_maps(tm.tmA, parent, LS.nodes_parent * LS.P_parent, np, b, m, LS.k, o16);
             if (rc != STTSM_OK) return rc;
             LevelInst& L = tm.L;
             L.parent = parent;
@@ -491,6 +522,7 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
             L.P_parent = LS.P_parent;
             L.P_out = LS.P_out;
             L.rows_per_parent = LS.P_out * s.R;
+            L.order16x8 = o16 ? 1 : 0;
             int64_t bp = 1;
             for (int a = 0; a <= STTSM_MAX_M; ++a) { L.bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
             const double lflops = (double)LS.nodes_out * (double)LS.P_out * (double)s.nbar * 2.0 * (double)s.bm * b;

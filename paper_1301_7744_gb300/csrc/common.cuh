@@ -54,10 +54,10 @@ struct Tile {
     int32_t inst;        // instance descriptor index (batched launches)
     int32_t parent;      // rank of the parent node among level d-1 nodes (0 at level 0)
     int32_t child_base;  // rank of the parent's first child among level d nodes
-    int32_t row0;        // first output row of the tile within the parent's rows
+    int32_t row0;        // first output row of the tile within the parent's rows (see pad0)
     int32_t col0;        // first output column (j index, = jbar * b + c)
     int32_t ncols;       // valid columns in this tile
-    int32_t pad0, pad1;
+    int32_t pad0, pad1;  // TMA-fed tiles: pad0 = 1 when the rows are 16 fastest x 8 next (plan.h)
 };
 
 // Everything a level kernel needs to know about one sttsm instance at one
@@ -79,6 +79,7 @@ struct LevelInst {
     int64_t rows_per_parent;  // P_out * R
     int32_t bpow[STTSM_MAX_M + 1];
     int32_t out_np;         // 0: FP32 output; else BF16 pieces per block [node][block][piece][b^m]
+    int32_t order16x8;      // TMA-fed tiles: rows row0 + (t mod 16) + b (t div 16) (see plan.h)
 };
 
 // Rows of a tile are mapped to (prefix block pr, row rr) by

@@ -184,8 +184,10 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 // positions whose runs are loaded atom by atom
                 int sl_ib = 0, sl_a = 0;
                 uint32_t amask = 0;
-                if (SW32)
+                const bool o16 = SW32 && I.order16x8;   // tile rows: 16 fastest x 8 next (one box per slice)
+                if (SW32 && !o16)
                     for (int q = 1; q <= I.k; ++q) amask |= atomwise_run(I.bpow[q]) ? (1u << q) : 0u;
+                const int o_f0 = rr0 % I.b, o_s0 = rr0 / I.b;
                 for (int ks = 0; ks < nk; ++ks) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                     const int k0 = ks * TC_KC;
@@ -208,7 +210,12 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                             const int q = gq & 7;
                             const int bp = (int)(((int64_t)t.parent * I.P_parent + (gq >> 3)) * NP);
                             const uint32_t dA = sA + (uint32_t)(h * NP * (S::A_PLANE / 2));
-                            if (q == 0) {
+                            if (o16) {
+                                // {a, f, r1, r2, block x piece} at q = 0, {f, a, r1, r2, ...} at q >= 1
+                                const int r1 = o_s0 % I.b, r2 = o_s0 / I.b;
+                                if (q == 0) tma_load_5d(dA, &TI.tmA[0], a0, o_f0, r1, r2, bp, full_bar(stage));
+                                else tma_load_5d(dA, &TI.tmA[q], o_f0, a0, r1, r2, bp, full_bar(stage));
+                            } else if (q == 0) {
                                 tma_load_3d(dA, &TI.tmA[0], a0, rr0, bp, full_bar(stage));
                             } else {
                                 const int bq = I.bpow[q];
@@ -274,7 +281,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 tc_fence_after();
                 int sl_ib = 0, sl_a = 0;
                 uint32_t amask = 0;
-                if (SW32)
+                if (SW32 && !I.order16x8)
                     for (int q = 1; q <= I.k; ++q) amask |= atomwise_run(I.bpow[q]) ? (1u << q) : 0u;
                 for (int ks = 0; ks < nk; ++ks) {
                     // A major-ness, atom layout and presence of the two 16-wide K slices
@@ -402,7 +409,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(d1_empty);
-            const int g = t.row0 + row;
+            const int g = t.row0 + (SW32 && I.order16x8 ? (row & 15) + I.b * (row >> 4) : row);
             if (active && g < I.rows_per_parent) {
                 const int pr = g / I.R, rr = g - pr * I.R;
                 const int b = I.b, bk = I.bpow[I.k];

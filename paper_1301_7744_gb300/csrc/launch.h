@@ -100,7 +100,9 @@ int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, i
 
 // Tensor maps of a BF16-piece parent array with nblocks stored blocks (all
 // nodes) for insertion positions q = 0..k of a level (see kernels_tma.cu).
-int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, int npiece, int b, int m, int k);
+// order16x8: the level's tiles are 16 fastest x 8 next rows (plan.h tma_order16x8).
+int make_a_tensor_maps(CUtensorMap* maps, const void* pieces, int64_t nblocks, int npiece, int b, int m, int k,
+                       bool order16x8 = false);
 
 // Builds the TMA descriptor of an X-piece array (box: TC_KC x box_rows x npiece).
 int make_x_tensor_map(CUtensorMap* map, const void* xpieces, int npiece, int rows, int Kp, int box_rows = TC_BN);

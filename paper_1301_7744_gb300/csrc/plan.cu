@@ -77,10 +77,29 @@ void build_level_G(const Shape& s, int d, std::vector<int32_t>& G)
             G[base + (size_t)(q * s.R + rr)] = (int32_t)(rr % bq + bq * s.b * (rr / bq));
 }
 
-void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles)
+bool tma_order16x8(const Shape& s, int d)
+{
+    if (!tc_tma_mode(s) || !tma_sw32(s) || s.m > 4 || s.m < 3 || s.b % 16 != 0 || (s.R / s.b) % 8 != 0) return false;
+    const int k = s.lv[d].k;
+    int64_t bq = s.b;
+    for (int q = 1; q <= k; ++q, bq *= s.b)
+        if (bq % 128 != 0 && 128 % bq != 0) return true;
+    return false;
+}
+
+void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles, bool order16x8)
 {
     const LevelShape& L = s.lv[d];
     const int64_t rows = L.P_out * s.R;
+    // first rows of the tiles of one parent: row0 + t, or blocks of 16 fastest x 8 next
+    std::vector<int64_t> starts;
+    if (order16x8) {
+        for (int64_t pr = 0; pr < L.P_out; ++pr)
+            for (int64_t s0 = 0; s0 < s.R / s.b; s0 += 8)
+                for (int64_t f0 = 0; f0 < s.b; f0 += 16) starts.push_back(pr * s.R + f0 + s.b * s0);
+    } else {
+        for (int64_t r0 = 0; r0 < rows; r0 += BM) starts.push_back(r0);
+    }
     int32_t u[STTSM_MAX_M];
     for (int64_t par = 0; par < L.nodes_parent; ++par) {
         int64_t children, child_base = 0;
@@ -97,7 +116,7 @@ void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std:
         int64_t w = BN;
         const int64_t nct = (ncols + BN - 1) / BN;
         if (BN >= 128 && nct > 1) w = ((ncols + nct - 1) / nct + 15) / 16 * 16;
-        for (int64_t r0 = 0; r0 < rows; r0 += BM) {
+        for (int64_t r0 : starts) {
             for (int64_t c0 = 0; c0 < ncols; c0 += w) {
                 Tile t;
                 t.inst = inst;
@@ -106,7 +125,8 @@ void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std:
                 t.row0 = (int32_t)r0;
                 t.col0 = (int32_t)c0;
                 t.ncols = (int32_t)(ncols - c0 < w ? ncols - c0 : w);
-                t.pad0 = t.pad1 = 0;
+                t.pad0 = order16x8 ? 1 : 0;
+                t.pad1 = 0;
                 tiles.push_back(t);
             }
         }
@@ -215,7 +235,8 @@ const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN, 
     for (int d = 0; d < m; ++d) {
         std::vector<Tile> tiles;
         std::vector<int32_t> G;
-        build_level_tiles(P->shape, d, BM, d == m - 1 ? bn_last : BN, 0, tiles);
+        build_level_tiles(P->shape, d, BM, d == m - 1 ? bn_last : BN, 0, tiles,
+                          BM == TC_BM && tma_order16x8(P->shape, d));
         build_level_G(P->shape, d, G);
         P->ntiles[d] = (int)tiles.size();
         for (const Tile& t : tiles) P->maxcols[d] = std::max(P->maxcols[d], (int)t.ncols);

@@ -57,10 +57,20 @@ inline bool tc_tma_mode(const Shape& s) { return !tc_small_mode(s) && s.b % 16 =
 inline bool tma_sw32_b(int b) { return !(b == 32 || b == 64 || b % 128 == 0); }
 inline bool tma_sw32(const Shape& s) { return tma_sw32_b(s.b); }
 
+// TMA-fed levels whose 128-row tiles are 16 values of the fastest row index
+// times 8 of the next (Tile::pad0 = 1): the 16-wide slice form (b = 48, 80,
+// 112, ...) with m <= 4, at levels where some insertion position q >= 1 has
+// runs of b^q rows that neither divide 128 nor are multiples of it.  Every A
+// box of such a tile is one TMA load whatever q is.
+bool tma_order16x8(const Shape& s, int d);
+
 // Host tile list and G table of level d (appended to the given vectors).
 // Tiles cover, for every parent node, P_out * R rows in steps of BM and the
-// parent's children * b columns in steps of BN.
-void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles);
+// parent's children * b columns in steps of BN; with order16x8 (BM = 128) a
+// tile's rows are row0 + (t mod 16) + b (t div 16), t < 128, instead of
+// row0 + t.
+void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles,
+                       bool order16x8 = false);
 // Number of tiles build_level_tiles emits for level d (counted, not built).
 int64_t level_tile_count(const Shape& s, int d, int BM, int BN);
 // G table of level d ([P_out][nbar]) followed by its offset table OFF

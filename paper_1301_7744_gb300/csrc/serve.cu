@@ -265,7 +265,7 @@ int admit(sttsm_serve_s* H, Req& R, const TableSet& T)
         // R64: the gathered kernel sums in FP64 at every level and the TMA kernel at
         // the last one, with tiles of at most 128 columns there
         const int bn = (H->r64 && !R.small && (!R.tma || d == s.m - 1)) ? R64_BN : box;
-        build_level_tiles(s, d, TC_BM, bn, 0, R.tiles[d]);
+        build_level_tiles(s, d, TC_BM, bn, 0, R.tiles[d], R.tma && tma_order16x8(s, d));
         const int32_t* G = (const int32_t*)(H->table_base + T.off + T.level_off[d]);
         const LevelShape& LS = s.lv[d];
         TcInst& T = R.inst[d];
@@ -300,7 +300,9 @@ int admit(sttsm_serve_s* H, Req& R, const TableSet& T)
             TmaInst& M = R.tinst[d];
             memset(&M, 0, sizeof(M));
             for (int xs = 0; xs < TMA_NX; ++xs) M.tmX[xs] = xmaps[xs];
-            if (make_a_tensor_maps(M.tmA, L.parent, LS.nodes_parent * LS.P_parent, H->np, s.b, s.m, LS.k) != STTSM_OK)
+            L.order16x8 = tma_order16x8(s, d) ? 1 : 0;
+            if (make_a_tensor_maps(M.tmA, L.parent, LS.nodes_parent * LS.P_parent, H->np, s.b, s.m, LS.k,
+                                   L.order16x8 != 0) != STTSM_OK)
                 return STTSM_ERR_CUDA;
             M.L = L;
         }

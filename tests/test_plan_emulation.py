@@ -47,9 +47,13 @@ def emulate(st, m, n, p, b, prec, A_bcss, X, nlev=None):
             assert np.array_equal(OFF[q], rrs % b ** q + b ** (q + 1) * (rrs // b ** q))
         kk = np.arange(nbar * b)
         ib, a = kk // b, kk % b
-        for inst, par, cb, row0, col0, ncols, _, _ in tiles:
+        for inst, par, cb, row0, col0, ncols, order16x8, _ in tiles:
             assert inst == 0 and 0 <= par < info["nodes_parent"] and 0 < ncols
-            g = row0 + np.arange(BM)
+            t = np.arange(BM)
+            # TMA-fed tiles of 16 fastest x 8 next rows (pad0 = 1), else consecutive rows
+            g = row0 + (t % 16 + b * (t // 16) if order16x8 else t)
+            if order16x8:
+                assert BM == 128 and (row0 % R) % b % 16 == 0 and g.max() // R == row0 // R
             g = g[g < rows_pp]
             assert g.size > 0
             pr, rr = g // R, g % R
@@ -75,7 +79,7 @@ def emulate(st, m, n, p, b, prec, A_bcss, X, nlev=None):
     return parent
 
 
-CASES = [(3, 24, 24, 8), (1, 10, 7, 4), (2, 9, 11, 3), (3, 17, 5, 6), (4, 13, 9, 4), (5, 7, 6, 2), (4, 20, 12, 5),
+CASES = [(3, 96, 96, 48), (3, 150, 100, 48), (3, 24, 24, 8), (1, 10, 7, 4), (2, 9, 11, 3), (3, 17, 5, 6), (4, 13, 9, 4), (5, 7, 6, 2), (4, 20, 12, 5),
          (3, 40, 40, 4), (2, 300, 260, 64), (6, 6, 5, 2), (3, 40, 33, 1), (2, 64, 64, 1), (4, 21, 21, 7),
          (3, 5, 3, 8), (2, 3, 10, 4), (8, 3, 2, 1), (7, 4, 3, 2), (6, 5, 4, 1),
          # degenerate: one entry, n = 1 < b, p = 1, m = 1 with n = p = 1
@@ -183,3 +187,16 @@ def test_fused_pair_only_for_short_shapes(st):
         st.sttsm_plan_pair(3, 40, 90, 4)          # p-bar b > 64
     with pytest.raises(st.SttsmError):
         st.sttsm_plan_pair(1, 10, 7, 4)           # one level: nothing to fuse
+
+
+def test_order16x8_only_where_runs_misalign(st):
+    """Tiles of 16 fastest x 8 next rows appear exactly at the TMA-fed levels of the
+    16-wide slice form whose runs of b^q rows (q >= 1) neither divide 128 nor are
+    multiples of it: b = 48 at levels 0 and 1 of m = 3, not at its last level and
+    not for b = 16, 32 or 64."""
+    for (m, n, p, b), want in (((3, 96, 96, 48), [1, 1, 0]), ((3, 96, 96, 16), [0, 0, 0]),
+                               ((3, 96, 96, 32), [0, 0, 0]), ((3, 130, 130, 64), [0, 0, 0])):
+        got = [int(st.sttsm_plan_level(m, n, p, b, st.STTSM_BF16X6, d)[0][:, 6].max()) for d in range(m)]
+        assert got == want, (m, n, p, b, got)
+    # the FP64 path keeps consecutive rows
+    assert st.sttsm_plan_level(3, 96, 96, 48, st.STTSM_FP64, 0)[0][:, 6].max() == 0
