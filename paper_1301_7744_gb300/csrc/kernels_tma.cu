@@ -19,7 +19,8 @@
 // which is how the permutation of App. A (permute before dgemm) becomes a choice
 // of tensor map and operand major-ness per stage instead of a data movement.
 //
-// CTA = 18 warps, one per SM, persistent over the tile list:
+// CTA = 18 warps, one per SM, persistent over the tile list (launches whose
+// tiles are all <= 64 columns: 10 warps with 8 epilogue warps, two CTAs per SM):
 //   warps 0-15  epilogue: D0 partials (x0*y0, restarted after the first 128
 //               contraction indices of a tile and then every 64) folded into FP32
 //               registers, D1 (cross products) added at the end of the tile; the
@@ -41,10 +42,6 @@ using namespace ptx;
 
 namespace {
 
-constexpr int T_THREADS = 576;
-constexpr int T_EPI_WARPS = 16;
-constexpr int T_MMA_WARP = 16;
-constexpr int T_TMA_WARP = 17;
 // D0 (x0*y0) restarts: the first group of a tile spans T_GS0 stages (room for
 // the epilogue to finish the previous tile's stores before the first drain),
 // the later ones T_GS stages
@@ -72,6 +69,9 @@ struct SmemT {
     static constexpr int NSTAGES = STAGES * STAGE / NSTAGE;
     static constexpr int MAXST = NSTAGES > STAGES ? NSTAGES : STAGES;
     static constexpr int BYTES = STAGES * STAGE + 1024 + 256;
+    // the two-CTAs-per-SM form for launches of tiles <= 64 columns (8 epilogue warps)
+    static constexpr int NSTAGES_P = NP == 3 ? 3 : 4;
+    static constexpr int BYTES_P = NSTAGES_P * NSTAGE + 1024 + 256;
 };
 
 // acc[0..63] += 64 consecutive TMEM columns of this warp's lanes from taddr
@@ -86,11 +86,12 @@ __device__ __forceinline__ void tmem_fold64(float* acc, uint32_t taddr)
     }
 }
 
-// acc[0..n) += n consecutive TMEM columns (n a multiple of 8, < 64)
+// acc[0..n) += n consecutive TMEM columns (n a multiple of 8, < MAXC)
+template <int MAXC = 64>
 __device__ __forceinline__ void tmem_fold_n(float* acc, uint32_t taddr, int n)
 {
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
+    for (int c = 0; c < MAXC / 8; ++c) {
         if (c * 8 >= n) break;
         float v[8];
         tmem_ld_32x32b_x8(taddr + c * 8, v);
@@ -114,18 +115,25 @@ __device__ __forceinline__ void tmem_fold32_f64(double* acc, uint32_t taddr)
 
 }  // namespace
 
-template <int NP, int OUT, bool SW32>
-__global__ void __launch_bounds__(T_THREADS, 1)
+// EW epilogue warps: 16 (one CTA per SM, all 512 TMEM columns, tiles up to 256
+// columns), or 8 for launches whose tiles are all <= 64 columns (two CTAs per
+// SM, 128 TMEM columns and three or four narrow stages each, so twice as many
+// tiles are in flight)
+template <int NP, int OUT, bool SW32, int EW>
+__global__ void __launch_bounds__((EW + 2) * 32, EW == 16 ? 1 : 2)
 level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restrict__ insts,
                  const Tile* __restrict__ tiles, int ntiles, int* status, int narrow)
 {
     using S = SmemT<NP>;
     constexpr int MAXST = S::MAXST;
-    const int STAGES = narrow ? S::NSTAGES : S::STAGES;
-    const int STAGE_BYTES = narrow ? S::NSTAGE : S::STAGE;
+    constexpr int EPIW = EW, MMAW = EW, TMAW = EW + 1;
+    constexpr uint32_t TCOLS = EW == 16 ? 512u : 128u;
+    constexpr uint32_t D0OFF = EW == 16 ? (uint32_t)TC_BN : 64u;
+    const int STAGES = EW == 16 ? (narrow ? S::NSTAGES : S::STAGES) : S::NSTAGES_P;
+    const int STAGE_BYTES = (narrow || EW != 16) ? S::NSTAGE : S::STAGE;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = (uint64_t*)(smem + S::STAGES * S::STAGE);
+    uint64_t* bars = (uint64_t*)(smem + (EW == 16 ? S::STAGES * S::STAGE : S::NSTAGES_P * S::NSTAGE));
     uint32_t* tmem_holder = (uint32_t*)(bars + 2 * MAXST + 4);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
@@ -141,15 +149,16 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
         mbar_init(d0_full, 1);
-        mbar_init(d0_empty, T_EPI_WARPS);
-        mbar_init(d1_empty, T_EPI_WARPS);
+        mbar_init(d0_empty, EPIW);
+        mbar_init(d1_empty, EPIW);
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
-    if (warp == T_MMA_WARP) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(smem_u32(tmem_holder)));
+    if (warp == MMAW) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_holder)), "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -157,9 +166,9 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
     const uint32_t tmem_d1 = tmem_base;
-    const uint32_t tmem_d0 = tmem_base + (uint32_t)TC_BN;
+    const uint32_t tmem_d0 = tmem_base + D0OFF;
 
-    if (warp == T_TMA_WARP) {
+    if (warp == TMAW) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             int stage = 0;
@@ -259,7 +268,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             }
         }
         __syncwarp();
-    } else if (warp == T_MMA_WARP) {
+    } else if (warp == MMAW) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             int stage = 0;
@@ -371,7 +380,8 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
         // FP32 register sums, or FP64 ones for C under the R64 precisions (32 columns
         // per thread: tiles of at most 128 columns)
         constexpr bool R64 = OUT == TMA_OUT_C64;
-        constexpr int AW = R64 ? 32 : 64;
+        constexpr int AW = (R64 || EW != 16) ? 32 : 64;
+        constexpr int PARTS = EW / 4;               // column parts of a tile (4 or 2)
         using AccT = typename std::conditional<R64, double, float>::type;
         AccT acc[AW];
         for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
@@ -382,7 +392,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             const int ngroups = d0_groups(nk);
             // (the FP32 writer of C keeps whole 64-column quarters: its rows are
             // contiguous, and longer runs per thread store faster)
-            const int cw = R64 ? 32 : OUT == TMA_OUT_C ? 64 : ((((t.ncols + 15) & ~15) + 3) / 4 + 7) & ~7;
+            const int cw = R64 ? 32 : OUT == TMA_OUT_C ? AW : ((((t.ncols + 15) & ~15) + PARTS - 1) / PARTS + 7) & ~7;
             const int colbase = cq * cw;
             const bool active = colbase < t.ncols;
 #pragma unroll
@@ -393,8 +403,10 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                 tc_fence_after();
                 if (active) {
                     if constexpr (R64) tmem_fold32_f64(acc, tmem_d0 + lane_off + (uint32_t)colbase);
-                    else if (cw == 64) tmem_fold64(acc, tmem_d0 + lane_off + (uint32_t)colbase);
-                    else tmem_fold_n(acc, tmem_d0 + lane_off + (uint32_t)colbase, cw);
+                    else if constexpr (AW == 64) {
+                        if (cw == 64) tmem_fold64(acc, tmem_d0 + lane_off + (uint32_t)colbase);
+                        else tmem_fold_n<64>(acc, tmem_d0 + lane_off + (uint32_t)colbase, cw);
+                    } else tmem_fold_n<AW + 8>(acc, tmem_d0 + lane_off + (uint32_t)colbase, cw);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -403,8 +415,10 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
             if (!ok) break;
             if (active) {
                 if constexpr (R64) tmem_fold32_f64(acc, tmem_d1 + lane_off + (uint32_t)colbase);
-                else if (cw == 64) tmem_fold64(acc, tmem_d1 + lane_off + (uint32_t)colbase);
-                else tmem_fold_n(acc, tmem_d1 + lane_off + (uint32_t)colbase, cw);
+                else if constexpr (AW == 64) {
+                    if (cw == 64) tmem_fold64(acc, tmem_d1 + lane_off + (uint32_t)colbase);
+                    else tmem_fold_n<64>(acc, tmem_d1 + lane_off + (uint32_t)colbase, cw);
+                } else tmem_fold_n<AW + 8>(acc, tmem_d1 + lane_off + (uint32_t)colbase, cw);
             }
             tc_fence_before();
             __syncwarp();
@@ -422,7 +436,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     // of a row are b^k apart inside a child's block
                     float* dst = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm + rowoff;
 #pragma unroll
-                    for (int e = 0; e < 64; ++e) {
+                    for (int e = 0; e < AW; ++e) {
                         if (e >= nvalid) break;
                         dst[(int64_t)bk * c] = acc[e];
                         if (++c == b) { c = 0; dst += I.P_out * I.bm; }
@@ -472,7 +486,7 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
                     const uint32_t sel = odd ? 0x3276u : 0x5410u;
                     const int64_t soff = odd ? (int64_t)bk - 1 : 0;
 #pragma unroll
-                    for (int e = 0; e < 64; e += 2) {
+                    for (int e = 0; e < AW; e += 2) {
                         if (e >= nvalid) break;
                         float2 x = make_float2(acc[e], acc[e + 1]);
 #pragma unroll
@@ -501,8 +515,8 @@ level_tma_kernel(const __grid_constant__ TmaInst inst0, const TmaInst* __restric
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == T_MMA_WARP) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem_base));
+    if (warp == MMAW) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_base), "r"(TCOLS));
     }
 }
 
@@ -567,10 +581,12 @@ int launch_split_bcss(const float* in, void* out, int64_t nblocks, int64_t bm, i
     return (int)cudaGetLastError();
 }
 
-template <int NP, int OUT, bool B>
+template <int NP, int OUT, bool B, int EW>
 static int launch_tma_variant(const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles, int grid,
                               int* d_status, int narrow, cudaStream_t s)
 {
+    constexpr int threads = (EW + 2) * 32;
+    constexpr int bytes = EW == 16 ? SmemT<NP>::BYTES : SmemT<NP>::BYTES_P;
     static std::mutex mu;
     static bool attr_set[64] = {};
     int dev = 0;
@@ -578,23 +594,28 @@ static int launch_tma_variant(const TmaInst& inst0, const TmaInst* d_insts, cons
     {
         std::lock_guard<std::mutex> lock(mu);
         if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-            const cudaError_t e = cudaFuncSetAttribute(level_tma_kernel<NP, OUT, B>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SmemT<NP>::BYTES);
+            const cudaError_t e = cudaFuncSetAttribute(level_tma_kernel<NP, OUT, B, EW>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
             if (e != cudaSuccess) return (int)e;
             attr_set[dev] = true;
         }
     }
-    level_tma_kernel<NP, OUT, B><<<grid, T_THREADS, SmemT<NP>::BYTES, s>>>(inst0, d_insts, d_tiles, ntiles, d_status,
-                                                                            narrow);
+    level_tma_kernel<NP, OUT, B, EW><<<grid, threads, bytes, s>>>(inst0, d_insts, d_tiles, ntiles, d_status, narrow);
     return (int)cudaGetLastError();
 }
 
+// Launches of tiles <= 64 columns run the two-CTAs-per-SM form (twice the grid).
 template <int NP, int OUT>
 static int launch_tma_b(bool sw32, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
                         int grid, int* d_status, int narrow, cudaStream_t s)
 {
-    return sw32 ? launch_tma_variant<NP, OUT, true>(inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s)
-               : launch_tma_variant<NP, OUT, false>(inst0, d_insts, d_tiles, ntiles, grid, d_status, narrow, s);
+    if (narrow) {
+        const int g2 = ntiles < 2 * grid ? ntiles : 2 * grid;
+        return sw32 ? launch_tma_variant<NP, OUT, true, 8>(inst0, d_insts, d_tiles, ntiles, g2, d_status, 1, s)
+                    : launch_tma_variant<NP, OUT, false, 8>(inst0, d_insts, d_tiles, ntiles, g2, d_status, 1, s);
+    }
+    return sw32 ? launch_tma_variant<NP, OUT, true, 16>(inst0, d_insts, d_tiles, ntiles, grid, d_status, 0, s)
+               : launch_tma_variant<NP, OUT, false, 16>(inst0, d_insts, d_tiles, ntiles, grid, d_status, 0, s);
 }
 
 int launch_level_tma(int npiece, const TmaInst& inst0, const TmaInst* d_insts, const Tile* d_tiles, int ntiles,
