@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16x6_r64", "bf16x3_r64"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
-    ap.add_argument("--workload", default="single", choices=["single", "m4", "abo", "batch", "serve"],
+    ap.add_argument("--workload", default="single", choices=["single", "m4", "abo", "batch", "serve", "symmetry"],
                     help="single: m=3 n=p=768 instance (default); m4: m=4 n=128 p=64 compressing instance; "
                          "abo: all modes but one on the m=3 n=p=768 instance; batch: 4096 mixed instances; "
                          "serve: Poisson stream")
@@ -64,6 +64,9 @@ def parse_args():
     ap.add_argument("--fused-tail", type=int, default=1, choices=[0, 1, 2],
                     help="short contractions' last two levels: 0 two launches, 1 fused in single calls "
                          "(library default), 2 fused in batch plans and serving too")
+    ap.add_argument("--inblock-sym", type=int, default=0, choices=[0, 1],
+                    help="short contractions: 1 computes the canonical entries of diagonal blocks only "
+                         "(sttsm_set_inblock_symmetry), 0 every entry (library default)")
     ap.add_argument("--no-configs", action="store_true",
                     help="leave the m4 / batch / serve short forms out of the default line")
     ap.add_argument("--configs-serve-seconds", type=float, default=10.0,
@@ -521,6 +524,7 @@ def run_m4(args, emit=True, short=False):
     __graft_entry__.build()
     import paper_1301_7744_gb300 as st
     st.sttsm_set_fused_tail(args.fused_tail)
+    st.sttsm_set_inblock_symmetry(args.inblock_sym)
     import synth
     import oracle
     m, n, p = 4, 128, 64
@@ -588,6 +592,7 @@ def run_abo(args):
     __graft_entry__.build()
     import paper_1301_7744_gb300 as st
     st.sttsm_set_fused_tail(args.fused_tail)
+    st.sttsm_set_inblock_symmetry(args.inblock_sym)
     import synth
     import oracle
     b = 64 if args.b == "auto" else int(args.b)
@@ -642,6 +647,7 @@ def run_batch(args, emit=True, short=False):
     __graft_entry__.build()
     import paper_1301_7744_gb300 as st
     st.sttsm_set_fused_tail(args.fused_tail)
+    st.sttsm_set_inblock_symmetry(args.inblock_sym)
     import synth
     prec = st.STTSM_BF16X6
     shapes = synth.batch_shapes(3, args.batch_count)
@@ -690,6 +696,7 @@ def run_batch(args, emit=True, short=False):
         tot_unfused, _ = time_steps(torch, lambda: plan_uf.run(ws), 3, 2)
         plan_uf.destroy()
         st.sttsm_set_fused_tail(args.fused_tail)
+        st.sttsm_set_inblock_symmetry(args.inblock_sym)
     clocks = ClockSampler()
     clocks.start()
     total_ms, per = time_steps(torch, lambda: plan.run(ws), steps, max(3, args.warmup))
@@ -801,6 +808,7 @@ def run_serve(args, emit=True, seconds=None, serve_prec=None):
     __graft_entry__.build()
     import paper_1301_7744_gb300 as st
     st.sttsm_set_fused_tail(args.fused_tail)
+    st.sttsm_set_inblock_symmetry(args.inblock_sym)
     import synth
     prec = prec_code(st, serve_prec or "bf16x6")
     seconds = float(seconds or args.serve_seconds)
@@ -926,8 +934,78 @@ def run_serve(args, emit=True, seconds=None, serve_prec=None):
     return line
 
 
+SYM_SHAPES = [(5, 64, 64, 16), (5, 64, 64, 8), (5, 64, 64, 4), (4, 64, 64, 16), (4, 64, 64, 8), (3, 64, 64, 32),
+              (3, 64, 64, 16), (5, 32, 32, 16), (4, 48, 48, 16)]
+
+
+def run_symmetry(args):
+    """Symmetry inside diagonal blocks (sttsm_set_inblock_symmetry) on single short-
+    contraction instances: per shape the time of one sttsm_bcss call (BF16X6) with the
+    mode off and on (CUDA events, 30 calls, best of two alternating rounds), the Tbl. 4
+    flops, the flops the mode's tiles issue (canonical rows x all columns x 2 n̄ b) and the
+    minimum of Sec. 6 (unique entries only, 2 n sum_d C(p+d, d+1) C(n+m-d-2, m-d-1)),
+    and the relative error against the oracle for the smallest shape with the mode on."""
+    import math
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_7744_gb300 as st
+    import synth
+    import oracle
+    prec = st.STTSM_BF16X6
+    out = {}
+    for (m, n, p, b) in SYM_SHAPES:
+        X = synth.x_gaussian(SEED_X, p, n)
+        d = torch.empty(n ** m, dtype=torch.float32, device="cuda")
+        synth.dev_sym_uniform_dense(d.data_ptr(), m, n, SEED_A, "f32", torch.cuda.current_stream().cuda_stream)
+        Ab = torch.empty(st.bcss_num_elems(m, n, b), dtype=torch.float32, device="cuda")
+        st.bcss_pack(d, Ab, m, n, b)
+        del d
+        dX = torch.from_numpy(xcol32(X)).cuda()
+        C = torch.empty(st.bcss_num_elems(m, p, b), dtype=torch.float32, device="cuda")
+        ws = st.workspace_tensor(m, n, p, b, prec)
+        best = {0: float("inf"), 1: float("inf")}
+        for sym in (0, 1, 0, 1):
+            st.sttsm_set_inblock_symmetry(sym)
+            tot, _ = time_steps(torch, lambda: st.sttsm_bcss(Ab, dX, m, n, p, b, C, prec, ws), 30, 5,
+                                per_step_events=False)
+            best[sym] = min(best[sym], tot / 30)
+        st.sttsm_set_inblock_symmetry(1)
+        nbar = -(-n // b)
+        issued = 0
+        for lv in range(m):
+            tiles, _, info = st.sttsm_plan_level(m, n, p, b, prec, lv)
+            rows = np.minimum(info["BM"], tiles[:, 7].astype(np.int64) - tiles[:, 3])
+            issued += int(2 * (rows * tiles[:, 5].astype(np.int64)).sum()) * nbar * b
+        st.sttsm_set_inblock_symmetry(0)
+        minimum = 2 * n * sum(math.comb(p + dd, dd + 1) * math.comb(n + m - dd - 2, m - dd - 1) for dd in range(m))
+        out[f"m{m}_n{n}_p{p}_b{b}"] = {"ms_off": best[0], "ms_on": best[1], "speedup": best[0] / best[1],
+                                       "tbl4_gflop": st.sttsm_flops(m, n, p, b) / 1e9,
+                                       "issued_gflop_on": issued / 1e9, "minimum_gflop": minimum / 1e9}
+    # accuracy with the mode on, smallest shape
+    m, n, p, b = min(SYM_SHAPES, key=lambda s: s[1] ** s[0])
+    A = synth.sym_uniform_dense(m, n, SEED_A)
+    X32 = synth.x_gaussian(SEED_X, p, n).astype(np.float32).astype(np.float64)
+    d = torch.from_numpy(A.astype(np.float32)).cuda()
+    Ab = torch.empty(st.bcss_num_elems(m, n, b), dtype=torch.float32, device="cuda")
+    st.bcss_pack(d, Ab, m, n, b)
+    C = torch.empty(st.bcss_num_elems(m, p, b), dtype=torch.float32, device="cuda")
+    st.sttsm_set_inblock_symmetry(1)
+    st.sttsm_bcss(Ab, torch.from_numpy(xcol32(X32)).cuda(), m, n, p, b, C, prec, st.workspace_tensor(m, n, p, b, prec))
+    torch.cuda.synchronize()
+    st.sttsm_set_inblock_symmetry(0)
+    ref = oracle.bcss_pack(oracle.sttsm_chain(A, X32, m), m, p, b)
+    err = float(np.linalg.norm(C.double().cpu().numpy() - ref) / np.linalg.norm(ref))
+    print(json.dumps({"metric": "sttsm single-call ms, in-block symmetry off / on", "unit": "ms",
+                      "higher_is_better": False, "dtype": "f32 (BF16X6 products)", "data": "synthetic",
+                      "results": out, "rel_err_on": {"shape": [m, n, p, b], "rel_fro": err}}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "symmetry":
+        return run_symmetry(args)
     if args.workload == "serve":
         return run_serve(args)
     if args.impl == "reference":
@@ -956,6 +1034,7 @@ def main():
             __graft_entry__.build()
     import paper_1301_7744_gb300 as st
     st.sttsm_set_fused_tail(args.fused_tail)
+    st.sttsm_set_inblock_symmetry(args.inblock_sym)
 
     prec = prec_code(st, args.prec)
     import synth

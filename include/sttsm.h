@@ -25,9 +25,9 @@
  *     the last block index varies slowest, the order of the paper's loops;
  *     for m = 2, b = 1 it is the element order pictured in Sec. 3.3).  A
  *     block is a dense b^m array in dimensional order.  Block entries that
- *     fall at an index >= n are padding and are zero.  Symmetry inside
- *     diagonal blocks is not exploited (Sec. 3.3): diagonal blocks are
- *     stored in full.
+ *     fall at an index >= n are padding and are zero.  Diagonal blocks are
+ *     stored in full (Sec. 3.3); by default every entry of them is computed,
+ *     and sttsm_set_inblock_symmetry computes their canonical entries only.
  *   - Device pointers unless stated otherwise.  The caller owns every
  *     buffer; the library never frees caller memory.  The library owns
  *     only small per-shape plans (tile lists) it caches in device memory.
@@ -326,6 +326,32 @@ int sttsm_set_small_kernel(int kind);
  * submitted later and batch plans created later.  STTSM_ERR_ARG otherwise. */
 int sttsm_set_fused_tail(int mode);
 
+/* Symmetry inside diagonal blocks (Sec. 3.3 and 5.3 store blocks with
+ * repeated block indices in full and compute all their entries).  With on = 1,
+ * split-precision levels of short contractions of order m <= 5 (n̄ b <= 64,
+ * run by the FP32 kernel) compute only the canonical entries of each stored
+ * block of T^(k):
+ * those whose full indices are non-decreasing within the k leading and
+ * within the m - k trailing modes, the modes among which T^(k) is symmetric.
+ * The temporaries (in the workspace) hold only those, and the next level reads
+ * each operand entry at its canonical position; the level that writes the
+ * result copies each canonical entry to every position of its block that
+ * equals it by symmetry, so C (or T^(1) of sttsm_bcss_all_but_one) keeps the
+ * BCSS layout with full blocks, every diagonal block exactly symmetric.  When b divides n and p the entries
+ * computed per level are C(n+k-1, k) C(p+m-k-1, m-k), the minimum flop count
+ * of Sec. 6 ("analysis relative to minimum"); the columns of the diagonal
+ * child block past the canonical ones are still multiplied and dropped.
+ * Canonical rows are not contiguous in memory, so loads and stores coalesce
+ * less than in the full computation: on GB300 the mode is faster only where
+ * blocks are large and few per mode (m = 5, n = 64, b = 16), slower on small b.
+ * Results agree with on = 0 to within rounding (different entries of a
+ * diagonal block come from the same sum instead of sums in different orders).
+ * The fused last two levels (sttsm_set_fused_tail) are not used while it is
+ * on.  Affects later sttsm_bcss calls, batch plans created later and requests
+ * submitted later; the allocation-free entry point sttsm_bcss_noalloc always
+ * computes every entry.  Default 0.  STTSM_ERR_ARG unless on is 0 or 1. */
+int sttsm_set_inblock_symmetry(int on);
+
 /* Device status word: 0 = fine; otherwise the code of the last device-side
  * failure (1 = bounded wait timed out).  Reading clears it. */
 int sttsm_device_status(void);
@@ -344,13 +370,30 @@ int sttsm_selftest_wait_timeout(double limit_ms);
  * writes T^(m-1-d), Fig. 5) for precision `prec` (which fixes the tile
  * shape).  Host buffers; pass NULL buffers to query the sizes.
  *   tiles:  ntiles x 8 int32 (inst, parent node, first child node, first row,
- *           first column, columns, 0, 0), capacity tiles_cap tiles;
+ *           first column, columns, pad0, pad1), capacity tiles_cap tiles;
+ *           pad0 = 1 for TMA-fed tiles of 16 fastest x 8 next rows; in the
+ *           in-block-symmetry mode pad0 = 2 | tie pattern of the parent's
+ *           blocks << 8 | its first block << 16, pad1 = the parent's canonical
+ *           rows, and "first row" counts canonical rows (sttsm_plan_sym_rows);
+ *           else 0, 0;
  *   G:      P_out x nbar int32 gather table, (rank << 3) | q, capacity G_cap;
  *   info:   9 int64: k, P_parent, P_out, rows per parent, parent nodes,
  *           child nodes, rows per block R = b^(m-1), b^m, tile rows BM.
  * Returns STTSM_ERR_NOMEM if a capacity is too small. */
 int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_t* tiles, int64_t tiles_cap,
                      int32_t* G, int64_t G_cap, int64_t* ntiles_out, int64_t* nG_out, int64_t* info);
+
+/* The canonical-row map of the in-block-symmetry mode (sttsm_set_inblock_symmetry)
+ * at level d for parent node `parent` (colex rank of its sorted tuple of d
+ * p-blocks; 0 at level 0): for rho = rho0 .. rho0 + count - 1, g_out[i] = the
+ * row pr * b^(m-1) + rr (the row map of sttsm_plan_level) of canonical row rho,
+ * or -1 past the parent's canonical rows, and tie_out[i] bit a set where modes
+ * a and a + 1 of that row hold the same block within one symmetric group.
+ * *rows_out = the parent's canonical rows.  Host buffers (any may be NULL).
+ * STTSM_ERR_UNSUPPORTED unless m <= 5, n̄ b <= 64 and p̄ < 65536; STTSM_ERR_ARG for an
+ * out-of-range level, parent or range. */
+int sttsm_plan_sym_rows(int m, int64_t n, int64_t p, int b, int d, int64_t parent, int64_t rho0, int64_t count,
+                        int64_t* g_out, uint32_t* tie_out, int64_t* rows_out);
 
 /* The units of the fused launch of levels m-2 and m-1 (sttsm_set_fused_tail)
  * for a short-contraction shape: ntiles x 8 int32 (0, parent node J of level

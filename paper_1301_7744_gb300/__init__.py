@@ -134,6 +134,10 @@ def _load():
     L.sttsm_plan_level.restype = i32
     L.sttsm_plan_pair.argtypes = [i32, i64, i64, i32, P, i64, P, P]
     L.sttsm_plan_pair.restype = i32
+    L.sttsm_set_inblock_symmetry.argtypes = [i32]
+    L.sttsm_set_inblock_symmetry.restype = i32
+    L.sttsm_plan_sym_rows.argtypes = [i32, i64, i64, i32, i32, i64, i64, i64, P, P, P]
+    L.sttsm_plan_sym_rows.restype = i32
     _lib = L
     return L
 
@@ -146,8 +150,8 @@ def exported_symbols() -> list[str]:
             "sttsm_autotune_b_measured", "sttsm_batch_plan_create", "sttsm_batch_workspace_size",
             "sttsm_batch_info", "sttsm_batch_run", "sttsm_batch_plan_destroy", "sttsm_batch", "sttsm_serve_create",
             "sttsm_serve_submit", "sttsm_serve_poll", "sttsm_serve_stats", "sttsm_serve_destroy",
-            "sttsm_bcss_noalloc", "sttsm_noalloc_selftest_wait_timeout", "sttsm_set_small_kernel", "sttsm_set_fused_tail", "sttsm_device_status", "sttsm_selftest_wait_timeout",
-            "sttsm_plan_level", "sttsm_plan_pair", "sttsm_profile_enable", "sttsm_profile_read"]
+            "sttsm_bcss_noalloc", "sttsm_noalloc_selftest_wait_timeout", "sttsm_set_small_kernel", "sttsm_set_fused_tail", "sttsm_set_inblock_symmetry", "sttsm_device_status", "sttsm_selftest_wait_timeout",
+            "sttsm_plan_level", "sttsm_plan_pair", "sttsm_plan_sym_rows", "sttsm_profile_enable", "sttsm_profile_read"]
 
 
 def _check(fn: str, rc: int) -> None:
@@ -455,6 +459,13 @@ def sttsm_set_fused_tail(mode: int) -> None:
     _check("sttsm_set_fused_tail", _load().sttsm_set_fused_tail(mode))
 
 
+def sttsm_set_inblock_symmetry(on: bool) -> None:
+    """Short contractions under split precisions: compute only the canonical entries of
+    diagonal blocks (full indices non-decreasing within each symmetric group) and copy
+    them to the rest of the block (on), or compute every entry (off, default)."""
+    _check("sttsm_set_inblock_symmetry", _load().sttsm_set_inblock_symmetry(int(on)))
+
+
 def sttsm_selftest_wait_timeout(limit_ms: float) -> int:
     """Runs the bounded-wait self-test; returns the status code (STTSM_ERR_TIMEOUT expected)."""
     return int(_load().sttsm_selftest_wait_timeout(float(limit_ms)))
@@ -490,6 +501,23 @@ def sttsm_plan_pair(m: int, n: int, p: int, b: int):
     tiles = np.zeros((nt.value, 8), dtype=np.int32)
     _check("sttsm_plan_pair", L.sttsm_plan_pair(m, n, p, b, tiles.ctypes.data, nt.value, None, None))
     return tiles, int(g.value)
+
+
+def sttsm_plan_sym_rows(m: int, n: int, p: int, b: int, d: int, parent: int, rho0: int = 0, count: int | None = None):
+    """Canonical-row map of the in-block-symmetry mode at level d for one parent node:
+    (g [count] int64 rows pr * b^(m-1) + rr, -1 past the end; tie [count] uint32; rows of
+    the parent).  count None: all of the parent's canonical rows from rho0."""
+    import numpy as np
+    L = _load()
+    rows = ctypes.c_int64(0)
+    _check("sttsm_plan_sym_rows", L.sttsm_plan_sym_rows(m, n, p, b, d, parent, 0, 0, None, None, ctypes.byref(rows)))
+    if count is None:
+        count = max(rows.value - rho0, 0)
+    g = np.zeros(count, dtype=np.int64)
+    tie = np.zeros(count, dtype=np.uint32)
+    _check("sttsm_plan_sym_rows", L.sttsm_plan_sym_rows(m, n, p, b, d, parent, rho0, count, g.ctypes.data,
+                                                        tie.ctypes.data, None))
+    return g, tie, int(rows.value)
 
 
 def sttsm_profile_enable(on: bool) -> None:

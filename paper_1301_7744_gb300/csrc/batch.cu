@@ -69,6 +69,7 @@ struct Instance {
     sttsm_desc desc;
     Shape shape;
     bool fused = false;         // last two levels in the fused launch
+    bool sym = false;           // canonical entries only (in-block symmetry, sym.cuh)
     size_t ws_bytes;
     size_t x_off, buf_off[2];   // offsets inside the instance's workspace slice
     int rows, Kp;
@@ -186,6 +187,7 @@ int bind_workspace(sttsm_batch_plan_s* P, char* ws)
                 memset(&li, 0, sizeof(li));
                 li.parent = dl == 0 ? I.desc.A : (const void*)(base + I.buf_off[(dl - 1) & 1]);
                 li.out = (dl == s.m - 1 || pairl) ? I.desc.C : (void*)(base + I.buf_off[dl & 1]);
+                li.sym_full = dl == s.m - 1 ? 1 : 0;
                 li.G = P->G.at(std::make_tuple(s.m, s.nbar, s.b, dl));
                 li.OFF = li.G + level_G_size(s, dl);
                 li.X = I.desc.X;
@@ -305,8 +307,9 @@ int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_
         I.buf_off[1] = off;
         off += up256((size_t)s.buf_elems[1] * esz);
         I.ws_bytes = std::max<size_t>(off, 256);
+        I.sym = !fp64 && sym_levels(s, prec);
         I.fused = !fp64 && !prec_r64(prec) && tc_small_mode(s) && small_kernel_kind() == 0 && fused_tail_in_batches() &&
-                  pair_mode(s);
+                  pair_mode(s) && !I.sym;
         I.cost = sttsm_flops(s.m, s.n, s.p, s.b);
         P->useful_flops += I.cost;
         if (ws_budget && I.ws_bytes > ws_budget) return STTSM_ERR_NOMEM;
@@ -356,7 +359,11 @@ int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_
                 if (I.fused && lv >= I.shape.m - 2) continue;   // in the pair launch
                 const int32_t e = (int32_t)L.inst_ids.size();
                 L.inst_ids.push_back(id);
-                build_level_tiles(I.shape, lv, BM, small ? TC_SMALL_BN : (prec_r64(prec) ? R64_BN : BN), e, tiles);
+                if (small && I.sym) {
+                    build_level_tiles_sym(I.shape, lv, BM, TC_SMALL_BN, e, tiles);
+                } else {
+                    build_level_tiles(I.shape, lv, BM, small ? TC_SMALL_BN : (prec_r64(prec) ? R64_BN : BN), e, tiles);
+                }
             }
             L.ntiles = (int)tiles.size();
             for (const Tile& t : tiles) L.maxcols = std::max(L.maxcols, (int)t.ncols);

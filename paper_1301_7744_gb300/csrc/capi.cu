@@ -6,6 +6,7 @@
 #include <vector>
 #include "launch.h"
 #include "plan.h"
+#include "sym.cuh"
 #include "sttsm.h"
 
 using namespace sttsm;
@@ -142,6 +143,13 @@ int small_kernel_kind() { return g_small_kind.load(); }
 std::atomic<int> g_fused_tail{1};
 bool fused_tail_enabled() { return g_fused_tail.load() != 0; }
 bool fused_tail_in_batches() { return g_fused_tail.load() == 2; }
+std::atomic<int> g_inblock_sym{0};
+bool inblock_sym_enabled() { return g_inblock_sym.load() != 0; }
+bool sym_levels(const Shape& s, int prec)
+{
+    return inblock_sym_enabled() && prec_npiece(prec) > 0 && tc_small_mode(s) &&
+           (small_kernel_kind() == 0 || prec_r64(prec)) && sym_shape_ok(s);
+}
 
 int* batch_status_word() { return status_dev(); }
 int peek_status_word() { return g_status_host ? __atomic_load_n(g_status_host, __ATOMIC_SEQ_CST) : 0; }
@@ -370,6 +378,47 @@ int sttsm_set_fused_tail(int mode)
     return STTSM_OK;
 }
 
+int sttsm_set_inblock_symmetry(int on)
+{
+    if (on != 0 && on != 1) return STTSM_ERR_ARG;
+    g_inblock_sym.store(on);
+    return STTSM_OK;
+}
+
+int sttsm_plan_sym_rows(int m, int64_t n, int64_t p, int b, int d, int64_t parent, int64_t rho0, int64_t count,
+                        int64_t* g_out, uint32_t* tie_out, int64_t* rows_out)
+{
+    Shape s;
+    int rc = make_shape(m, n, p, b, &s);
+    if (rc != STTSM_OK) return rc;
+    if (!sym_shape_ok(s)) return STTSM_ERR_UNSUPPORTED;
+    if (d < 0 || d >= m || parent < 0 || parent >= s.lv[d].nodes_parent || rho0 < 0 || count < 0) return STTSM_ERR_ARG;
+    SymTab T;
+    sym_tab_fill(T, 0, 1);
+    uint32_t pattern = 0;
+    if (d > 0) {
+        int32_t u[STTSM_MAX_M];
+        colex_unrank(parent, d, u);
+        for (int t = 0; t + 1 < d; ++t)
+            if (u[t] == u[t + 1]) pattern |= 1u << t;
+    }
+    const int k = s.lv[d].k, Kp = (int)(s.nbar * b);
+    const int64_t rows = sym_parent_rows(T, m, k, b, Kp, pattern);
+    if (rows_out) *rows_out = rows;
+    int32_t bpow[STTSM_MAX_M + 1];
+    int64_t bp = 1;
+    for (int a = 0; a <= STTSM_MAX_M; ++a) { bpow[a] = (int32_t)(bp < ((int64_t)1 << 31) ? bp : 0); bp *= b; }
+    for (int64_t i = 0; i < count; ++i) {
+        uint32_t tie = 0;
+        const int64_t rho = rho0 + i;
+        uint32_t iblk = 0;
+        const int64_t g = rho < rows ? sym_row(T, m, k, b, Kp, s.R, bpow, pattern, rho, &tie, &iblk) : -1;
+        if (g_out) g_out[i] = g;
+        if (tie_out) tie_out[i] = tie;
+    }
+    return STTSM_OK;
+}
+
 int sttsm_profile_enable(int on)
 {
     std::lock_guard<std::mutex> lock(g_prof_mu);
@@ -410,7 +459,10 @@ int sttsm_plan_level(int m, int64_t n, int64_t p, int b, int prec, int d, int32_
     if (prec_r64(prec) && (d == m - 1 || gathered) && BN > R64_BN) BN = R64_BN;
     std::vector<Tile> tl;
     std::vector<int32_t> g;
-    build_level_tiles(s, d, BM, BN, 0, tl, !fp64 && tma_order16x8(s, d));
+    if (!fp64 && sym_levels(s, prec))
+        build_level_tiles_sym(s, d, BM, BN, 0, tl);
+    else
+        build_level_tiles(s, d, BM, BN, 0, tl, !fp64 && tma_order16x8(s, d));
     build_level_G(s, d, g);
     if (ntiles_out) *ntiles_out = (int64_t)tl.size();
     if (nG_out) *nG_out = (int64_t)g.size();
@@ -481,7 +533,9 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
     const bool gathered = !fp64 && !small && !tc_tma_mode(s);
     const int BM = fp64 ? 64 : TC_BM;
     const int BN = fp64 ? 64 : small ? TC_SMALL_BN : (r64 && gathered) ? R64_BN : TC_BN;
-    const DevPlan* P = get_dev_plan(m, n, p, b, BM, BN, r64 && BN > R64_BN ? R64_BN : BN);
+    // in-block symmetry: canonical entries only (short contractions, FP32 kernel)
+    const bool sym = !fp64 && sym_levels(s, prec);
+    const DevPlan* P = get_dev_plan(m, n, p, b, BM, BN, r64 && BN > R64_BN ? R64_BN : BN, sym);
     if (!P) return STTSM_ERR_NOMEM;
     char* ws = (char*)workspace;
     void* bufs[2] = {ws + w.buf0, ws + w.buf1};
@@ -547,13 +601,14 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
         if (rc != STTSM_OK) return rc;
     }
     // short contractions in FP32: the last two levels in one launch, T^(1) in shared memory
-    const bool pair = small && small_kernel_kind() == 0 && fused_tail_enabled() && nlev == m && P->d_pair && !r64;
+    const bool pair = small && small_kernel_kind() == 0 && fused_tail_enabled() && nlev == m && P->d_pair && !r64 && !sym;
     for (int d = 0; d < nlev; ++d) {
         const LevelShape& LS = s.lv[d];
         LevelInst& L = ti.L;
         const bool fused = pair && d == m - 2;
         L.parent = d == 0 ? A : bufs[(d - 1) & 1];
         L.out = (d == nlev - 1 || fused) ? C : bufs[d & 1];
+        L.sym_full = d == nlev - 1 ? 1 : 0;
         L.G = P->d_G[d];
         L.OFF = P->d_G[d] + level_G_size(s, d);
         L.X = X;

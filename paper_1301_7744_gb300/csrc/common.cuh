@@ -80,6 +80,8 @@ struct LevelInst {
     int32_t bpow[STTSM_MAX_M + 1];
     int32_t out_np;         // 0: FP32 output; else BF16 pieces per block [node][block][piece][b^m]
     int32_t order16x8;      // TMA-fed tiles: rows row0 + (t mod 16) + b (t div 16) (see plan.h)
+    int32_t sym_full;       // in-block-symmetry tiles (sym.cuh): 1 where out is the call's result
+                            // (every entry written), 0 for a temporary (canonical entries only)
 };
 
 // Rows of a tile are mapped to (prefix block pr, row rr) by

@@ -6,6 +6,7 @@
 #include <type_traits>
 #include <mutex>
 #include "common.cuh"
+#include "sym.cuh"
 #include "launch.h"
 
 namespace sttsm {
@@ -291,9 +292,20 @@ int launch_split_x_batch(const SplitDesc* d_desc, int count, int blocks, int npi
 // are latency-bound (batches and serving of small instances).
 constexpr int S32_ROWS = 128, S32_COLS = 64, S32_K = 64;
 
+// Tiles in the in-block-symmetry mode (sym.cuh): tile row t is the parent's
+// canonical row rho = row0 + t, at row g[t] = pr * R + rr of the full row map
+// (-1 past the parent's canonical rows), tie[t] its runs of equal blocks,
+// blk[t] its i blocks (8 bits each).
+struct S32Sym {
+    SymTab tab;
+    int32_t g[S32_ROWS];
+    uint32_t tie[S32_ROWS];
+    uint32_t blk[S32_ROWS];
+};
 struct S32Stage {
-    float A[S32_K][S32_ROWS];         // A[kk][t]: operand of output row row0 + t
+    float A[S32_K][S32_ROWS];         // A[kk][t]: operand of output row row0 + t (canonical row g[t])
     float X[S32_K][S32_COLS];         // X[kk][c] = chi_{col0 + c, kk}, zero outside the tile / X
+    S32Sym sym;
 };
 constexpr int S32_CTAS_PER_SM = 4;
 constexpr size_t S32_SMEM = sizeof(S32Stage);
@@ -430,13 +442,75 @@ __device__ __forceinline__ void s32_issue_a(S32Stage& S, const LevelInst& I, con
     for (int kk = I.Ktot; kk < Kc; ++kk) S.A[kk][threadIdx.x] = 0.f;
 }
 
+// Operand row of a tile in the in-block-symmetry mode.  The parent holds the
+// canonical entries of its blocks only (a temporary written in this mode; A
+// has them all), so every operand entry is read at its canonical position:
+// contraction offset a joins, at parent mode q, the run of the e parent modes
+// q+1 .. q+e whose blocks equal ibar (their offsets r_0 <= ... <= r_{e-1} are
+// the row's i offsets at modes q .. q+e-1); sorted, the r_i < a move down one
+// mode and a moves up p = #{r_i < a} modes:
+//     off_q(rr) + sum_{i<p} r_i (b^{q+i} - b^{q+i+1}) + a b^{q+p}.
+// Blocks that join no run (e = 0) take the plain strided copy (strides known at
+// compile time for B > 0, as in s32_issue_a).
+template <int B>
+__device__ __noinline__ void s32_issue_a_sym(S32Stage& S, const LevelInst& I, const Tile& t, int Kc)
+{
+    const int g = S.sym.g[threadIdx.x];
+    if (g >= 0) {
+        const int R = I.R, b = B > 0 ? B : I.b, nbar = I.nbar, k = I.k;
+        const int64_t bm = I.bm;
+        const int pr = g / R, rr = g - pr * R;
+        const float* pbase = (const float*)I.parent + (int64_t)t.parent * I.P_parent * bm;
+        const int32_t* Grow = I.G + (int64_t)pr * nbar;
+        const uint32_t iblk = S.sym.blk[threadIdx.x];
+        int32_t io[STTSM_MAX_M];
+        {
+            int rem = rr;
+            for (int x = 0; x < k; ++x) {
+                const int q2 = rem / b;
+                io[x] = rem - q2 * b;
+                rem = q2;
+            }
+        }
+        for (int ib = 0; ib < nbar; ++ib) {
+            const int32_t gq = __ldg(Grow + ib);
+            const int q = gq & 7;
+            const float* src = pbase + (int64_t)(gq >> 3) * bm + __ldg(I.OFF + q * R + rr);
+            int e = 0;
+            while (q + e < k && (int)((iblk >> (8 * (q + e))) & 0xff) == ib) ++e;
+            const uint32_t d0 = s32_smem(&S.A[ib * b][threadIdx.x]);
+            if (e == 0 && B > 0) {
+                if (q == 0) s32_copy_block<(B > 0 ? B : 1), 1>(d0, src);
+                else s32_copy_q<(B > 0 ? B : 1)>(d0, src, q);
+                continue;
+            }
+            int p = 0, corr = 0;
+            for (int a = 0; a < b; ++a) {
+                while (p < e && io[q + p] < a) {
+                    corr += io[q + p] * (I.bpow[q + p] - I.bpow[q + p + 1]);
+                    ++p;
+                }
+                s32_cp4(d0 + S32_KROW * a, src + corr + a * I.bpow[q + p], 4);
+            }
+        }
+    }
+    for (int kk = I.Ktot; kk < Kc; ++kk) S.A[kk][threadIdx.x] = 0.f;
+}
+
 template <typename Desc>
 __device__ __forceinline__ void s32_issue(S32Stage& S, const Desc* insts, const LevelInst& inst0, const Tile& t,
                                           bool with_x)
 {
     const LevelInst& I = insts ? level_of(insts, t.inst) : inst0;
     const int Kc = (I.Ktot + 3) & ~3;
-    switch (I.b) {
+    if (sym_tile(t.pad0)) {
+        switch (I.b) {
+        case 4: s32_issue_a_sym<4>(S, I, t, Kc); break;
+        case 8: s32_issue_a_sym<8>(S, I, t, Kc); break;
+        case 16: s32_issue_a_sym<16>(S, I, t, Kc); break;
+        default: s32_issue_a_sym<0>(S, I, t, Kc); break;
+        }
+    } else switch (I.b) {
     case 4: s32_issue_a<4>(S, I, t, Kc); break;
     case 8: s32_issue_a<8>(S, I, t, Kc); break;
     case 16: s32_issue_a<16>(S, I, t, Kc); break;
@@ -467,13 +541,244 @@ __device__ __forceinline__ uint64_t s32_dup(float a)
     return r;
 }
 
+// In-block symmetry: the entry of column cc of a canonical row (block prefix
+// pr, offsets o of the modes != k, tie bits of the row) goes to every position
+// of its child block that equals it by symmetry; the columns of the diagonal
+// child (jb = u_0) beyond the offset of mode k+1 are not canonical and are
+// dropped (their canonical entries are another row's).
+__device__ __noinline__ void s32_sym_put(const LevelInst& I, const Tile& t, int pr, int64_t rowoff, int32_t* o,
+                                         uint32_t tie, int cc, float v)
+{
+    const int b = I.b, k = I.k;
+    const int jb = cc / b, c = cc - jb * b;
+    const bool diag = k < I.m - 1 && jb == sym_u0(t.pad0);
+    if (diag && c > o[k + 1]) return;
+    // The range checks here never fail (every offset is a permutation of in-block
+    // offsets of a block of this tile's children); they keep a broken invariant from
+    // writing outside the output block.
+    if (pr >= I.P_out || (k < I.m - 1 && jb > sym_u0(t.pad0))) return;
+    float* blk = (float*)I.out + (((int64_t)t.child_base + jb) * I.P_out + pr) * I.bm;
+    const uint32_t tb = tie | (diag ? 1u << k : 0u);
+    if (tb == 0) {
+        const int64_t a = rowoff + (int64_t)I.bpow[k] * c;
+        if (a >= 0 && a < I.bm) blk[a] = v;
+        return;
+    }
+    o[k] = c;
+    for (int a = 0; a < I.m; ++a)
+        if (o[a] < 0 || o[a] >= b) return;
+    // every distinct permutation of o inside the runs of tb (m <= 5: at most 5! = 120)
+    int guard = 0;
+    for (;;) {
+        int64_t off = 0;
+        for (int a = 0; a < I.m; ++a) off += (int64_t)o[a] * I.bpow[a];
+        if (off >= 0 && off < I.bm) blk[off] = v;
+        if (++guard > 120) return;
+        bool adv = false;
+        for (int a = 0; a < I.m && !adv;) {
+            int hi = a + 1;
+            while (hi < I.m && ((tb >> (hi - 1)) & 1)) ++hi;
+            if (hi - a > 1) adv = sym_next_perm(o, a, hi);
+            a = hi;
+        }
+        if (!adv) break;
+    }
+}
+
+// Offsets of the modes != k of row rr (row digit a is mode a below k, a + 1 above).
+__device__ __forceinline__ void s32_row_digits(const LevelInst& I, int rr, int32_t* o)
+{
+    int rem = rr;
+    const int b = I.b, lb = (b & (b - 1)) == 0 ? __ffs(b) - 1 : -1;
+    for (int a = 0; a < I.m; ++a) {
+        if (a == I.k) { o[a] = 0; continue; }
+        const int q = lb >= 0 ? rem >> lb : rem / b;
+        o[a] = rem - q * b;
+        rem = q;
+    }
+}
+
+// One canonical row of a tile in the in-block-symmetry mode (sym.cuh), stored
+// from the registers of the thread that computed it.  For every mirror of the
+// row (its offsets permuted inside each run of equal blocks, mode k apart;
+// m <= 5 gives at most SYM_MAXMIR = 4! of them) the columns of the children
+// other than the diagonal one go to the mirror row as in the full computation
+// (4 at a time for b a power of two >= 4).  The diagonal child (jb = u_0, whose
+// mode k joins the run of modes k+1 .. k+gr): a canonical column c <= o_{k+1}
+// goes to the mirror row and to every position where c swaps places with the
+// offset w of one mode j of that run, offset + c b^j + w (b^k - b^j) -- these
+// swaps and the row's permutations give every arrangement of the run;
+// columns c > o_{k+1} are another row's mirrors and are dropped.
+constexpr int SYM_MAXMIR = 24;
+
+__device__ __forceinline__ void s32_sym_diag(float* row, const LevelInst& I, const int32_t* q, int gr, int bk, int cl,
+                                             float val)
+{
+    row[cl * bk] = val;
+    for (int j = 1; j <= gr; ++j) {
+        const int bj = I.bpow[I.k + j];
+        row[cl * bj + q[I.k + j] * (bk - bj)] = val;
+    }
+}
+
+template <int TC>
+__device__ __forceinline__ void s32_sym_store_row(const float (&v)[TC], const LevelInst& I, const Tile& t, int g,
+                                                  uint32_t tie, int cfirst, int nvalid)
+{
+    const int m = I.m, k = I.k, b = I.b, bk = I.bpow[k];
+    const int pr = g / I.R, rr = g - pr * I.R;
+    int32_t q[STTSM_MAX_M];
+    s32_row_digits(I, rr, q);
+    const int jbd = k < m - 1 ? sym_u0(t.pad0) : -1;
+    int gr = 0;
+    if (k < m - 1) {
+        gr = 1;
+        while (k + gr < m - 1 && ((tie >> (k + gr)) & 1)) ++gr;
+    }
+    const int ok1 = k < m - 1 ? q[k + 1] : 0;
+    const int64_t child_step = (int64_t)I.P_out * I.bm;
+    const float* base = (const float*)I.out + ((int64_t)t.child_base * I.P_out + pr) * I.bm;
+    const bool pow2 = b >= 4 && (b & (b - 1)) == 0;
+    const int lb = pow2 ? __ffs(b) - 1 : 0;
+    for (int mir = 0; mir < SYM_MAXMIR; ++mir) {
+        int32_t ro = 0;
+        for (int x = 0; x < m; ++x)
+            if (x != k) ro += q[x] * I.bpow[x];
+        float* row = (float*)base + ro;
+        if (pow2) {
+#pragma unroll
+            for (int e = 0; e < TC; e += 4) {
+                if (e >= nvalid) break;
+                const int cc = cfirst + e, jb = cc >> lb, c0 = cc & (b - 1);
+                float* d = row + (int64_t)jb * child_step;
+                if (jb != jbd) {
+                    d += (int64_t)bk * c0;
+                    if (bk == 1) {
+                        *(float4*)d = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                    } else {
+                        d[0] = v[e];
+                        d[bk] = v[e + 1];
+                        d[2 * bk] = v[e + 2];
+                        d[3 * bk] = v[e + 3];
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (c0 + u <= ok1) s32_sym_diag(d, I, q, gr, bk, c0 + u, v[e + u]);
+                }
+            }
+        } else {
+            int jb = cfirst / b, c = cfirst - jb * b;
+#pragma unroll
+            for (int e = 0; e < TC; ++e) {
+                if (e < nvalid) {
+                    float* d = row + (int64_t)jb * child_step;
+                    if (jb != jbd) d[(int64_t)bk * c] = v[e];
+                    else if (c <= ok1) s32_sym_diag(d, I, q, gr, bk, c, v[e]);
+                }
+                if (++c == b) { c = 0; ++jb; }
+            }
+        }
+        bool adv = false;   // next mirror: next permutation of the first run that has one
+        for (int x = 0; x < m && !adv;) {
+            int hi = x + 1;
+            while (hi < m && ((tie >> (hi - 1)) & 1)) ++hi;
+            if (hi - x > 1) adv = sym_next_perm(q, x, hi);
+            x = hi;
+        }
+        if (!adv) break;
+    }
+}
+
+// A temporary of the in-block-symmetry mode: the canonical entries of one row
+// only (the next level reads those), the columns of the diagonal child past the
+// offset of mode k+1 dropped.
+template <int TC>
+__device__ __forceinline__ void s32_sym_store_canon(const float (&v)[TC], const LevelInst& I, const Tile& t, int g,
+                                                    int cfirst, int nvalid)
+{
+    const int b = I.b, k = I.k, bk = I.bpow[k];
+    const int jbd = k < I.m - 1 ? sym_u0(t.pad0) : -1;
+    const int64_t child_step = (int64_t)I.P_out * I.bm;
+    const int pr = g / I.R, rr = g - pr * I.R;
+    const int ok1 = (rr / bk) % b;   // offset of mode k+1 (row digit k)
+    float* row = (float*)I.out + ((int64_t)t.child_base * I.P_out + pr) * I.bm + __ldg(I.OFF + k * I.R + rr);
+    if (b >= 4 && (b & (b - 1)) == 0) {
+        const int lb = __ffs(b) - 1;
+#pragma unroll
+        for (int e = 0; e < TC; e += 4) {
+            if (e >= nvalid) break;
+            const int cc = cfirst + e, jb = cc >> lb, c0 = cc & (b - 1);
+            float* d = row + (int64_t)jb * child_step + (int64_t)bk * c0;
+            if (jb != jbd) {
+                if (bk == 1) {
+                    *(float4*)d = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                } else {
+                    d[0] = v[e];
+                    d[bk] = v[e + 1];
+                    d[2 * bk] = v[e + 2];
+                    d[3 * bk] = v[e + 3];
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (c0 + u <= ok1) d[u * bk] = v[e + u];
+            }
+        }
+        return;
+    }
+    int jb = cfirst / b, c = cfirst - jb * b;
+#pragma unroll
+    for (int e = 0; e < TC; ++e) {
+        if (e < nvalid && (jb != jbd || c <= ok1)) row[(int64_t)jb * child_step + (int64_t)bk * c] = v[e];
+        if (++c == b) { c = 0; ++jb; }
+    }
+}
+
+// The rows of this thread (as s32_compute_store distributes them), whose results
+// it parked in its own cells of the operand stage: a separate function, so the
+// full computation's register allocation does not carry these stores.  The
+// call's result gets every entry (s32_sym_store_row), a temporary its canonical
+// entries (s32_sym_store_canon).
+template <int TC, int TR>
+__device__ __noinline__ void s32_sym_store(const S32Stage& S, const LevelInst& I, const Tile& t, int r0, int part,
+                                           int cfirst, int nvalid)
+{
+    constexpr int RSTEP = S32_ROWS / TR;
+#pragma unroll 1
+    for (int j = 0; j < TR; ++j) {
+        const int rowi = r0 + j * RSTEP;
+        const int g = S.sym.g[rowi];
+        if (g < 0) continue;
+        float v[TC];
+#pragma unroll
+        for (int e = 0; e < TC; ++e) v[e] = S.A[part * TC + e][rowi];
+        if (I.sym_full) s32_sym_store_row<TC>(v, I, t, g, S.sym.tie[rowi], cfirst, nvalid);
+        else s32_sym_store_canon<TC>(v, I, t, g, cfirst, nvalid);
+    }
+}
+
+// This thread's canonical row of a tile in the in-block-symmetry mode.
+__device__ __noinline__ void s32_sym_row(S32Stage& S, const LevelInst& I, const Tile& t)
+{
+    const int64_t rho = (int64_t)t.row0 + threadIdx.x;
+    uint32_t tie = 0, iblk = 0;
+    int64_t gg = rho < t.pad1
+                     ? sym_row(S.sym.tab, I.m, I.k, I.b, I.Ktot, I.R, I.bpow, sym_pattern(t.pad0), rho, &tie, &iblk)
+                     : -1;
+    if (gg >= I.rows_per_parent) gg = -1;   // never (the map stays inside the parent's rows)
+    S.sym.g[threadIdx.x] = (int32_t)gg;
+    S.sym.tie[threadIdx.x] = tie;
+    S.sym.blk[threadIdx.x] = iblk;
+}
+
 // Rows times the tile's X block, then the scatter into the children's blocks:
 // output (child cb + jb, block pr) at in-block offset OFF[k][rr] + b^k c.
 // A thread computes TR rows (t mod 128/TR, + 128/TR, ...) times NC/TR columns
 // (part t / (128/TR)), so every X value read from shared memory feeds TR
 // products; column pairs go through the two-lane FMA.
 template <int NC, int TR>
-__device__ __forceinline__ void s32_compute_store(const S32Stage& S, const LevelInst& I, const Tile& t)
+__device__ __forceinline__ void s32_compute_store(S32Stage& S, const LevelInst& I, const Tile& t)
 {
     constexpr int TC = NC / TR, RSTEP = S32_ROWS / TR;
     const int r0 = threadIdx.x % RSTEP, part = threadIdx.x / RSTEP;
@@ -505,6 +810,20 @@ __device__ __forceinline__ void s32_compute_store(const S32Stage& S, const Level
     const int b = I.b, bk = I.bpow[I.k];
     const int cfirst = t.col0 + part * TC;
     const int nvalid = t.ncols - part * TC;
+    if (sym_tile(t.pad0)) {
+        __syncthreads();   // every thread is done reading the operand stage
+#pragma unroll
+        for (int j = 0; j < TR; ++j)
+#pragma unroll
+            for (int e = 0; e < TC / 2; ++e) {
+                float lo, hi;
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[j][e]));
+                S.A[part * TC + 2 * e][r0 + j * RSTEP] = lo;   // this thread's own cells
+                S.A[part * TC + 2 * e + 1][r0 + j * RSTEP] = hi;
+            }
+        s32_sym_store<TC, TR>(S, I, t, r0, part, cfirst, nvalid);
+        return;
+    }
     if (b >= 4 && (b & (b - 1)) == 0) {
         // b a power of two >= 4: a thread's columns start on a multiple of 4 and
         // the tile's width is a multiple of b, so every group of 4 columns lies
@@ -567,11 +886,14 @@ __device__ __forceinline__ void s32_compute_store_r64(const S32Stage& S, const L
 {
     constexpr int CW = NC < 16 ? NC : 16;
     const int r = threadIdx.x;
-    const int g = t.row0 + r;
-    if (g >= I.rows_per_parent) return;
+    const bool sym = sym_tile(t.pad0);
+    const int g = sym ? S.sym.g[r] : t.row0 + r;
+    if (g < 0 || g >= I.rows_per_parent) return;
     const int Kc = (I.Ktot + 3) & ~3;
     const int b = I.b;
     const int pr = g / I.R, rr = g - pr * I.R;
+    int32_t o[STTSM_MAX_M];
+    if (sym) s32_row_digits(I, rr, o);
     float* row = (float*)I.out + ((int64_t)t.child_base * I.P_out + pr) * I.bm + __ldg(I.OFF + I.k * I.R + rr);
     const int64_t child_step = (int64_t)I.P_out * I.bm;
 #pragma unroll 1
@@ -610,6 +932,10 @@ __device__ __forceinline__ void s32_compute_store_r64(const S32Stage& S, const L
         for (int e = 0; e < CW; ++e) {
             const int cc = t.col0 + c0 + e;
             if (c0 + e >= t.ncols) break;
+            if (sym) {
+                s32_sym_put(I, t, pr, __ldg(I.OFF + I.k * I.R + rr), o, S.sym.tie[r], cc, (float)dacc[e]);
+                continue;
+            }
             const int jb = cc / b, c = cc - jb * b;
             row[(int64_t)jb * child_step + c] = (float)dacc[e];
         }
@@ -623,6 +949,7 @@ level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Ti
 {
     extern __shared__ __align__(16) unsigned char s32_raw[];
     S32Stage& S = *(S32Stage*)s32_raw;
+    bool tab_ready = false;   // binomial table of the symmetry mode, filled at the CTA's first such tile
     // row groups of one parent node share their X block; it stays in shared
     // memory while the CTA's next tile has the same one
     int x_inst = -1, x_col0 = -1, x_ncols = -1;
@@ -631,6 +958,14 @@ level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Ti
         const LevelInst& I = insts ? level_of(insts, t.inst) : inst0;
         const bool new_x = t.inst != x_inst || t.col0 != x_col0 || t.ncols != x_ncols;
         x_inst = t.inst; x_col0 = t.col0; x_ncols = t.ncols;
+        if (sym_tile(t.pad0)) {
+            if (!tab_ready) {
+                sym_tab_fill(S.sym.tab, threadIdx.x, blockDim.x);
+                __syncthreads();
+                tab_ready = true;
+            }
+            s32_sym_row(S, I, t);   // read by the other threads after the barrier below
+        }
         s32_issue(S, insts, inst0, t, new_x);
         s32_commit();
         s32_wait_all();
@@ -790,3 +1125,4 @@ int launch_level_fp64(const LevelInst& inst0, const LevelInst* d_insts, const Ti
 }
 
 }  // namespace sttsm
+

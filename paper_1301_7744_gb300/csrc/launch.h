@@ -45,7 +45,9 @@ int launch_level_tc_r64(int npiece, const TcInst& inst0, const TcInst* d_insts, 
 // FP32 CUDA-core kernel for short contractions (n̄ b <= 64): tiles of 128 rows
 // x <= 64 columns, X read from the instance's FP32 X (LevelInst::X).
 // r64: instances at their last level (k = 0) add the FP32 sums of their
-// contraction blocks in FP64 (the R64 precisions).
+// contraction blocks in FP64 (the R64 precisions).  Tiles built by
+// build_level_tiles_sym (Tile::pad0 = SYM_TILE) compute canonical entries only
+// (in-block symmetry, sym.cuh); a launch may mix both kinds.
 int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
                            int num_sms, cudaStream_t s, int r64 = 0);
 int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s,
@@ -60,6 +62,14 @@ int launch_level_pair_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int nti
 // in single calls (mode >= 1), and in batch plans and serving (mode 2).
 bool fused_tail_enabled();
 bool fused_tail_in_batches();
+
+// Whether split-precision levels of short-contraction shapes compute canonical
+// entries only (sttsm_set_inblock_symmetry; sym.cuh): the switch is on, the
+// FP32 short-contraction kernel runs them and the shape fits the tile
+// encoding (sym_shape_ok).
+bool inblock_sym_enabled();
+struct Shape;
+bool sym_levels(const Shape& s, int prec);
 
 // Kernel for short contractions under the split precisions: 0 = FP32 CUDA-core
 // kernel (default), 1 = tcgen05 small-tile kernel (sttsm_set_small_kernel).

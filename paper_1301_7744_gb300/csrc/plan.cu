@@ -5,6 +5,7 @@
 #include <tuple>
 #include "launch.h"
 #include "plan.h"
+#include "sym.cuh"
 #include "sttsm.h"
 
 namespace sttsm {
@@ -133,6 +134,49 @@ void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std:
     }
 }
 
+// m <= 5: a row then has at most 4! = 24 mirrors, the length of the store's list.
+bool sym_shape_ok(const Shape& s) { return s.m <= 5 && s.nbar * s.b <= 64 && s.b <= 64 && s.pbar < 65536; }
+
+void build_level_tiles_sym(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles)
+{
+    const LevelShape& L = s.lv[d];
+    SymTab T;
+    sym_tab_fill(T, 0, 1);
+    const int Kp = (int)(s.nbar * s.b);
+    int32_t u[STTSM_MAX_M];
+    for (int64_t par = 0; par < L.nodes_parent; ++par) {
+        int64_t children, child_base = 0;
+        uint32_t pattern = 0;
+        int u0 = 0;
+        if (d == 0) {
+            children = s.pbar;
+        } else {
+            colex_unrank(par, d, u);   // parent (jbar_{k+1} <= ... <= jbar_{m-1})
+            children = (int64_t)u[0] + 1;
+            u0 = u[0];
+            for (int t = 0; t < d; ++t) child_base += binom_small((int64_t)u[t] + t + 1, t + 2);
+            for (int t = 0; t + 1 < d; ++t)
+                if (u[t] == u[t + 1]) pattern |= 1u << t;
+        }
+        const int64_t rows = sym_parent_rows(T, s.m, L.k, s.b, Kp, pattern);
+        const int64_t ncols = children * s.b;
+        for (int64_t r0 = 0; r0 < rows; r0 += BM) {
+            for (int64_t c0 = 0; c0 < ncols; c0 += BN) {
+                Tile t;
+                t.inst = inst;
+                t.parent = (int32_t)par;
+                t.child_base = (int32_t)child_base;
+                t.row0 = (int32_t)r0;
+                t.col0 = (int32_t)c0;
+                t.ncols = (int32_t)(ncols - c0 < BN ? ncols - c0 : BN);
+                t.pad0 = SYM_TILE | (int32_t)(pattern << 8) | (int32_t)((uint32_t)u0 << 16);
+                t.pad1 = (int32_t)rows;
+                tiles.push_back(t);
+            }
+        }
+    }
+}
+
 int64_t level_tile_count(const Shape& s, int d, int BM, int BN)
 {
     const LevelShape& L = s.lv[d];
@@ -203,7 +247,7 @@ void build_pair_tiles(const Shape& s, int32_t inst, std::vector<Tile>& tiles)
 
 namespace {
 std::mutex g_mu;
-std::map<std::tuple<int, int, int64_t, int64_t, int, int, int, int>, DevPlan*> g_plans;
+std::map<std::tuple<int, int, int64_t, int64_t, int, int, int, int, bool>, DevPlan*> g_plans;
 
 void free_plan(DevPlan* P)
 {
@@ -216,12 +260,12 @@ void free_plan(DevPlan* P)
 }
 }  // namespace
 
-const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN, int bn_last)
+const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN, int bn_last, bool sym)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     if (bn_last <= 0) bn_last = BN;
-    auto key = std::make_tuple(dev, m, n, p, b, BM, BN, bn_last);
+    auto key = std::make_tuple(dev, m, n, p, b, BM, BN, bn_last, sym);
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) return it->second;
@@ -235,8 +279,11 @@ const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN, 
     for (int d = 0; d < m; ++d) {
         std::vector<Tile> tiles;
         std::vector<int32_t> G;
-        build_level_tiles(P->shape, d, BM, d == m - 1 ? bn_last : BN, 0, tiles,
-                          BM == TC_BM && tma_order16x8(P->shape, d));
+        if (sym)
+            build_level_tiles_sym(P->shape, d, BM, d == m - 1 ? bn_last : BN, 0, tiles);
+        else
+            build_level_tiles(P->shape, d, BM, d == m - 1 ? bn_last : BN, 0, tiles,
+                              BM == TC_BM && tma_order16x8(P->shape, d));
         build_level_G(P->shape, d, G);
         P->ntiles[d] = (int)tiles.size();
         for (const Tile& t : tiles) P->maxcols[d] = std::max(P->maxcols[d], (int)t.ncols);

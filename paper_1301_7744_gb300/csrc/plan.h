@@ -71,6 +71,13 @@ bool tma_order16x8(const Shape& s, int d);
 // row0 + t.
 void build_level_tiles(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles,
                        bool order16x8 = false);
+// Tiles of level d in the in-block-symmetry mode (sym.cuh): for every parent
+// node its canonical rows rho in steps of BM times the parent's children * b
+// columns in steps of BN; pad0 = SYM_TILE | tie pattern << 8 | u_0 << 16,
+// pad1 = the parent's canonical rows.  For short-contraction shapes of order
+// m <= 5 only (nbar b <= 64, pbar < 65536: sym_shape_ok).
+bool sym_shape_ok(const Shape& s);
+void build_level_tiles_sym(const Shape& s, int d, int BM, int BN, int32_t inst, std::vector<Tile>& tiles);
 // Number of tiles build_level_tiles emits for level d (counted, not built).
 int64_t level_tile_count(const Shape& s, int d, int BM, int BN);
 // G table of level d ([P_out][nbar]) followed by its offset table OFF
@@ -105,6 +112,7 @@ struct DevPlan {
 // on allocation failure.  Thread-safe.  The first call for a shape allocates
 // and copies synchronously (do it before any stream capture).  bn_last (0 =
 // BN): tile width bound of the last level.
-const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN, int bn_last = 0);
+// sym: level tiles in the in-block-symmetry mode (build_level_tiles_sym).
+const DevPlan* get_dev_plan(int m, int64_t n, int64_t p, int b, int BM, int BN, int bn_last = 0, bool sym = false);
 
 }  // namespace sttsm

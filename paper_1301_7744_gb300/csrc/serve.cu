@@ -112,6 +112,7 @@ struct Req {
     bool small = false;
     bool tma = false;           // TMA-fed kernel: A split once into pieces, temporaries as pieces
     bool fused = false;         // levels m-2 and m-1 in one step (the fused short-contraction kernel)
+    bool sym = false;           // canonical entries only (in-block symmetry, sym.cuh)
     size_t a_off = 0;
     int state = Q_QUEUED;
     int level = 0;              // next level to launch
@@ -265,7 +266,10 @@ int admit(sttsm_serve_s* H, Req& R, const TableSet& T)
         // R64: the gathered kernel sums in FP64 at every level and the TMA kernel at
         // the last one, with tiles of at most 128 columns there
         const int bn = (H->r64 && !R.small && (!R.tma || d == s.m - 1)) ? R64_BN : box;
-        build_level_tiles(s, d, TC_BM, bn, 0, R.tiles[d], R.tma && tma_order16x8(s, d));
+        if (R.sym)
+            build_level_tiles_sym(s, d, TC_BM, bn, 0, R.tiles[d]);
+        else
+            build_level_tiles(s, d, TC_BM, bn, 0, R.tiles[d], R.tma && tma_order16x8(s, d));
         const int32_t* G = (const int32_t*)(H->table_base + T.off + T.level_off[d]);
         const LevelShape& LS = s.lv[d];
         TcInst& T = R.inst[d];
@@ -274,6 +278,7 @@ int admit(sttsm_serve_s* H, Req& R, const TableSet& T)
         LevelInst& L = T.L;
         L.parent = d == 0 ? (R.tma ? (const void*)(base + R.a_off) : R.d.A) : (const void*)(base + R.buf_off[(d - 1) & 1]);
         L.out = d == s.m - 1 ? R.d.C : (void*)(base + R.buf_off[d & 1]);
+        L.sym_full = d == s.m - 1 ? 1 : 0;
         L.out_np = (R.tma && d < s.m - 1) ? H->np : 0;
         L.G = G;
         L.OFF = G + level_G_size(s, d);
@@ -584,7 +589,8 @@ int sttsm_serve_submit(void* h, const sttsm_desc* d, uint64_t* ticket)
     if (rc != STTSM_OK) return rc;
     R.small = tc_small_mode(R.s);
     R.tma = tc_tma_mode(R.s);
-    R.fused = R.small && !H->r64 && small_kernel_kind() == 0 && fused_tail_in_batches() && pair_mode(R.s);
+    R.sym = sym_levels(R.s, H->prec);
+    R.fused = R.small && !H->r64 && small_kernel_kind() == 0 && fused_tail_in_batches() && pair_mode(R.s) && !R.sym;
     R.rows = (int)(R.s.pbar * R.s.b);
     R.Kp = (int)(((R.s.nbar * R.s.b) + 7) / 8 * 8);
     R.x_off = 0;
