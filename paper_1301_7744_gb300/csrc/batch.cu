@@ -79,6 +79,7 @@ struct Instance {
 struct LevelLaunch {
     int ntiles = 0;
     int maxcols = 0;              // widest tile
+    int sym = 0;                  // some tiles in the in-block-symmetry mode
     Tile* d_tiles = nullptr;
     void* d_insts = nullptr;      // TcInst[] or LevelInst[]
     std::vector<int> inst_ids;    // instance of every descriptor
@@ -238,7 +239,7 @@ int enqueue(sttsm_batch_plan_s* P, cudaStream_t s)
             // most 128 wide) and the FP32 kernel does so at each instance's last level
             const int rc = fp64 ? launch_level_fp64(dummy.L, (const LevelInst*)L.d_insts, L.d_tiles, L.ntiles, sms, s)
                          : (mode && (small_kernel_kind() == 0 || r64))
-                             ? launch_level_small_f32_tc(ti, L.d_tiles, L.ntiles, sms, s, r64 ? 1 : 0)
+                             ? launch_level_small_f32_tc(ti, L.d_tiles, L.ntiles, sms, s, r64 ? 1 : 0, L.sym)
                          : mode ? launch_level_tc_small(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, s)
                          : r64 ? launch_level_tc_r64(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, L.maxcols, s)
                                : launch_level_tc(np, dummy, ti, L.d_tiles, L.ntiles, sms, P->status, s);
@@ -361,6 +362,7 @@ int sttsm_batch_plan_create(const sttsm_desc* d, int count, int prec, size_t ws_
                 L.inst_ids.push_back(id);
                 if (small && I.sym) {
                     build_level_tiles_sym(I.shape, lv, BM, TC_SMALL_BN, e, tiles);
+                    L.sym = 1;
                 } else {
                     build_level_tiles(I.shape, lv, BM, small ? TC_SMALL_BN : (prec_r64(prec) ? R64_BN : BN), e, tiles);
                 }

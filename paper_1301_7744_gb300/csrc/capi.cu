@@ -635,7 +635,8 @@ int run_chain(const void* A, const void* X, int m, int64_t n, int64_t p, int b, 
         if (fp64) rc = cuda_err(launch_level_fp64(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream));
         // the R64 precisions: the last level sums in FP64 (the FP32 kernel for short contractions)
         else if (small && (small_kernel_kind() == 0 || r64))
-            rc = cuda_err(launch_level_small_f32(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream, r64 && d == m - 1));
+            rc = cuda_err(launch_level_small_f32(L, nullptr, P->d_tiles[d], P->ntiles[d], sms, stream, r64 && d == m - 1,
+                                                 sym ? 1 : 0));
         else if (small) rc = cuda_err(launch_level_tc_small(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, stream));
         else if (r64)
             rc = cuda_err(launch_level_tc_r64(np, ti, nullptr, P->d_tiles[d], P->ntiles[d], sms, st, P->maxcols[d], stream));

@@ -2,6 +2,7 @@
 // the FP32 -> BF16-piece split of X, and the plain FP64 level kernel of the
 // algorithm-by-blocks (Fig. 5 with Thm. 1).
 #include <cuda_bf16.h>
+#include <cstddef>
 #include <cstring>
 #include <type_traits>
 #include <mutex>
@@ -97,6 +98,74 @@ __global__ void bcss_pack_kernel(const T* __restrict__ dense, T* __restrict__ bc
     }
 }
 
+// The same work units for the common case (16-byte accesses, b^M < 2^31,
+// M * nbar colex-rank terms fit in shared memory), with the order M a template
+// parameter: every thread unranks the unit's block tuple itself from the
+// tabulated terms C(v + t, t + 1) (a binary search per position; no barrier
+// per unit), and the per-entry loops have exactly M steps.
+template <typename T, int M>
+__global__ void __launch_bounds__(256)
+bcss_pack_vec_kernel(const T* __restrict__ dense, T* __restrict__ bcss, int64_t n, int b, int nbar, int64_t nblocks,
+                     uint32_t bm)
+{
+    using W = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    constexpr int V = 16 / sizeof(T);
+    extern __shared__ int64_t pk_ctab[];   // pk_ctab[t * nbar + v] = C(v + t, t + 1)
+    for (int i = threadIdx.x; i < M * nbar; i += blockDim.x) {
+        const int t = i / nbar, v = i - t * nbar;
+        pk_ctab[i] = binom_small((int64_t)v + t, t + 1);
+    }
+    __syncthreads();
+    const bool bpow2 = (b & (b - 1)) == 0;
+    const int lb = bpow2 ? __ffs(b) - 1 : 0;
+    int64_t npow[M];
+    {
+        int64_t w = 1;
+#pragma unroll
+        for (int a = 0; a < M; ++a) { npow[a] = w; w *= n; }
+    }
+    int top = 1;   // largest power of two <= nbar
+    while (top * 2 <= nbar) top *= 2;
+    const uint32_t nchunk = (bm + (uint32_t)PACK_CHUNK - 1) / (uint32_t)PACK_CHUNK;
+    for (int64_t w = blockIdx.x; w < nblocks * nchunk; w += gridDim.x) {
+        const int64_t blk = w / nchunk;
+        const uint32_t c0 = (uint32_t)(w - blk * nchunk) * (uint32_t)PACK_CHUNK;
+        const uint32_t c1 = c0 + (uint32_t)PACK_CHUNK < bm ? c0 + (uint32_t)PACK_CHUNK : bm;
+        int32_t tup[M];
+        {
+            int64_t r = blk;
+#pragma unroll
+            for (int t = M - 1; t >= 0; --t) {
+                const int64_t* ct = pk_ctab + t * nbar;
+                int v = 0;
+                for (int step = top; step > 0; step >>= 1)
+                    if (v + step < nbar && ct[v + step] <= r) v += step;
+                tup[t] = v;
+                r -= ct[v];
+            }
+        }
+        T* dst = bcss + blk * (int64_t)bm;
+#pragma unroll 2
+        for (uint32_t e = c0 + threadIdx.x * V; e < c1; e += blockDim.x * V) {
+            uint32_t r = e;
+            int64_t off = 0;
+            bool inside = true;
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                const uint32_t q = bpow2 ? r >> lb : r / (uint32_t)b;
+                const int64_t i = (int64_t)tup[a] * b + (int64_t)(r - q * (uint32_t)b);
+                r = q;
+                inside = inside && (i < n);
+                off += i * npow[a];
+            }
+            W v;
+            if (inside) v = *(const W*)(dense + off);
+            else memset(&v, 0, sizeof(v));
+            *(W*)(dst + e) = v;
+        }
+    }
+}
+
 // One thread per dense entry: sort the indices (a compare-exchange network on
 // registers), read the canonical entry.  The colex rank of the sorted block
 // tuple sums C(v_t + t, t + 1) over its positions t; with tab the CTA first
@@ -170,6 +239,254 @@ __global__ void bcss_unpack_kernel(const T* __restrict__ bcss, T* __restrict__ d
     }
 }
 
+// Unpack by tiles (m >= 2).  A work unit is one dense block B (block indices
+// B_0 .. B_{m-1}, any order), a TX x TX tile of in-block offsets along dense
+// mode 0 (x) and along mode a* (y; the mode >= 1 holding the smallest block),
+// and a group of S consecutive slabs of the other m - 2 offsets.  Every entry
+// reads from the stored block sort(B) (rank once per unit), at the offsets of
+// its sorted full indices (the canonical entry; a sort of M values per entry).
+// The reads go along whichever of x and y is stored mode 0 (B_0 the strict
+// minimum: x; else y), so a warp reads consecutive stored entries, through a
+// padded shared tile; the writes go along x, consecutive dense entries.  The
+// unit first tabulates its slabs' fixed offsets (8 bits each, b <= 256) and
+// their share of the dense address in shared memory.  The order M is a
+// template parameter so the per-entry loops and the sorting network have
+// exactly M (M (M-1) / 2) steps; in-block offsets are 32-bit (b^M < 2^31).
+constexpr int UT_MAX_SLABS = 256;
+
+template <typename T, int M>
+__global__ void __launch_bounds__(256)
+bcss_unpack_tiled_kernel(const T* __restrict__ bcss, T* __restrict__ dense, int64_t n, int b, int nbar, int64_t bm,
+                         int TX, int ntx, int slabs, int S, uint32_t ngrp, uint32_t total_units, int vec4)
+{
+    extern __shared__ __align__(16) unsigned char ut_raw[];
+    int64_t* ctab = (int64_t*)ut_raw;                             // ctab[t * nbar + v] = C(v + t, t + 1)
+    int64_t* slab_addr = ctab + (size_t)M * nbar;                 // [S] dense-address share of the slab's offsets
+    uint64_t* slab_off = (uint64_t*)(slab_addr + UT_MAX_SLABS);   // [S] offsets of modes != 0, a* (8 bits each)
+    T* tile = (T*)(slab_off + UT_MAX_SLABS);                      // [S][TX][TX + 1]
+    for (int i = threadIdx.x; i < M * nbar; i += blockDim.x) {
+        const int t = i / nbar, v = i - t * nbar;
+        ctab[i] = binom_small((int64_t)v + t, t + 1);
+    }
+    const int P = TX + 1;
+    const bool tpow2 = (TX & (TX - 1)) == 0;
+    const int ltx = tpow2 ? __ffs(TX) - 1 : 0;
+    const bool bpow2 = (b & (b - 1)) == 0;
+    const int lb = bpow2 ? __ffs(b) - 1 : 0;
+    const uint32_t per_block = (uint32_t)(ntx * ntx) * ngrp;
+    for (uint32_t u = blockIdx.x; u < total_units; u += gridDim.x) {
+        const uint32_t blin = u / per_block;
+        uint32_t rem = u - blin * per_block;
+        const uint32_t tt = rem / ngrp;
+        const int slab0 = (int)(rem - tt * ngrp) * S;
+        const int tyi = (int)tt / ntx, txi = (int)tt - tyi * ntx;
+        const int nslab = slabs - slab0 < S ? slabs - slab0 : S;
+        int32_t B[M], sB[M];
+        {
+            uint32_t r = blin;
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                const uint32_t q = r / (uint32_t)nbar;
+                B[a] = (int32_t)(r - q * (uint32_t)nbar);
+                sB[a] = B[a];
+                r = q;
+            }
+        }
+        int as = 1, Bas = B[1];
+#pragma unroll
+        for (int a = 2; a < M; ++a)
+            if (B[a] < Bas) { as = a; Bas = B[a]; }
+        const bool read_x = B[0] < Bas;
+#pragma unroll
+        for (int i = 0; i < M - 1; ++i)
+#pragma unroll
+            for (int j = 0; j < M - 1 - i; ++j) {
+                const int32_t lo = min(sB[j], sB[j + 1]), hi = max(sB[j], sB[j + 1]);
+                sB[j] = lo;
+                sB[j + 1] = hi;
+            }
+        int64_t nas = 1;   // n^a*
+        for (int a = 0; a < as; ++a) nas *= n;
+        const int x0 = txi * TX, y0 = tyi * TX;
+        const int nx = b - x0 < TX ? b - x0 : TX, ny = b - y0 < TX ? b - y0 : TX;
+        const int64_t bx = (int64_t)B[0] * b + x0, by = (int64_t)Bas * b + y0;
+        const int xlim = n - bx < nx ? (int)(n - bx) : nx;   // x < xlim: index < n
+        const int ylim = n - by < ny ? (int)(n - by) : ny;
+        const int64_t base = bx + by * nas;
+        __syncthreads();   // ctab filled (first unit) / the previous unit is done with the tables and the tile
+        if (xlim <= 0 || ylim <= 0) continue;   // uniform in the CTA
+        int64_t rank = 0;
+#pragma unroll
+        for (int a = 0; a < M; ++a) rank += ctab[a * nbar + sB[a]];
+        const T* src = bcss + rank * bm;
+        // no repeated block index: mode a goes to stored mode pi(a) = #{B_a' < B_a} for
+        // every entry, so the stored offset is linear in the tile's coordinates
+        uint32_t wpi[M];   // b^pi(a)
+        bool tiefree = true;
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            int pa = 0;
+#pragma unroll
+            for (int a2 = 0; a2 < M; ++a2) {
+                pa += B[a2] < B[a] ? 1 : 0;
+                tiefree = tiefree && (a2 == a || B[a2] != B[a]);
+            }
+            uint32_t w = 1;
+            for (int t = 0; t < pa; ++t) w *= (uint32_t)b;
+            wpi[a] = w;
+        }
+        const bool fast = vec4 && tiefree;
+        for (int sl = threadIdx.x; sl < nslab; sl += blockDim.x) {
+            uint32_t sr = (uint32_t)(slab0 + sl);
+            int64_t share = 0, w = 1;
+            uint64_t offs = 0;
+            bool ok = true;
+            int c = 0;
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                if (a > 0 && a != as) {
+                    const uint32_t q = bpow2 ? sr >> lb : sr / (uint32_t)b;
+                    const int off = (int)(sr - q * (uint32_t)b);
+                    sr = q;
+                    const int64_t i = (int64_t)B[a] * b + off;
+                    ok = ok && i < n;
+                    share += i * w;
+                    if (fast) offs += (uint64_t)((uint32_t)off * wpi[a]);
+                    else offs |= (uint64_t)off << (8 * c);
+                    ++c;
+                }
+                w *= n;
+            }
+            slab_addr[sl] = ok ? share : -1;
+            slab_off[sl] = offs;   // fast: the fixed modes' share of the stored offset
+        }
+        __syncthreads();
+        if (fast) {
+            // 4 consecutive entries per access (b, n, TX multiples of 4; 16-byte aligned arrays)
+            const int TX4 = TX >> 2;
+            const int cnt4 = nslab * TX * TX4;
+            const uint32_t corner = (uint32_t)x0 * wpi[0] + (uint32_t)y0 * wpi[as];   // the tile's origin
+            if (read_x) {
+                // x is stored mode 0 and dense mode 0: a straight copy along x
+                const uint32_t wy = wpi[as];
+                for (int e = threadIdx.x; e < cnt4; e += blockDim.x) {
+                    const int sl = e / (TX * TX4), w = e - sl * TX * TX4;
+                    const int y = w / TX4, x = (w - y * TX4) * 4;
+                    const int64_t sa = slab_addr[sl];
+                    if (x >= xlim || y >= ylim || sa < 0) continue;
+                    const float4 v = *(const float4*)((const float*)src + corner + (uint32_t)slab_off[sl] + x + y * wy);
+                    *(float4*)((float*)dense + base + sa + x + (int64_t)y * nas) = v;
+                }
+                continue;
+            }
+            // y is stored mode 0: 4 consecutive y in, transposed in the tile, 4 consecutive x out
+            const uint32_t wx = wpi[0];
+            for (int e = threadIdx.x; e < cnt4; e += blockDim.x) {
+                const int sl = e / (TX * TX4), w = e - sl * TX * TX4;
+                const int x = w / TX4, y = (w - x * TX4) * 4;
+                if (x >= xlim || y >= ylim || slab_addr[sl] < 0) continue;
+                const float4 v = *(const float4*)((const float*)src + corner + (uint32_t)slab_off[sl] + x * wx + y);
+                float* tp = (float*)tile + (sl * TX + x) * P + y;
+                tp[0] = v.x;
+                tp[1] = v.y;
+                tp[2] = v.z;
+                tp[3] = v.w;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < cnt4; e += blockDim.x) {
+                const int sl = e / (TX * TX4), w = e - sl * TX * TX4;
+                const int y = w / TX4, x = (w - y * TX4) * 4;
+                const int64_t sa = slab_addr[sl];
+                if (x >= xlim || y >= ylim || sa < 0) continue;
+                const float* tp = (const float*)tile + (sl * TX + x) * P + y;
+                *(float4*)((float*)dense + base + sa + x + (int64_t)y * nas) = make_float4(tp[0], tp[P], tp[2 * P], tp[3 * P]);
+            }
+            continue;
+        }
+        // in-block offset of sorted full indices s_t: sum_t s_t b^t - sum_t sB_t b^(t+1),
+        // below b^M < 2^31; the terms wrap modulo 2^32 (unsigned), the difference is exact
+        uint32_t bmul[M];   // b^t
+        {
+            uint32_t w = 1;
+#pragma unroll
+            for (int a = 0; a < M; ++a) { bmul[a] = w; w *= (uint32_t)b; }
+        }
+        uint32_t sbase = 0;
+#pragma unroll
+        for (int a = 0; a < M; ++a) sbase += (uint32_t)sB[a] * (uint32_t)b * bmul[a];
+        const int cnt = nslab * TX * TX;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            int sl, w;
+            if (tpow2) { sl = e >> (2 * ltx); w = e & (TX * TX - 1); }
+            else { sl = e / (TX * TX); w = e - sl * TX * TX; }
+            const int fa = tpow2 ? (w & (TX - 1)) : w % TX, fb = tpow2 ? (w >> ltx) : w / TX;
+            const int x = read_x ? fa : fb, y = read_x ? fb : fa;
+            if (x >= xlim || y >= ylim || slab_addr[sl] < 0) continue;
+            const uint64_t offs = slab_off[sl];
+            int32_t f[M];
+            int c = 0;
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                if (a == 0) {
+                    f[a] = (int32_t)bx + x;
+                } else if (a == as) {
+                    f[a] = (int32_t)by + y;
+                } else {
+                    f[a] = B[a] * b + (int)((offs >> (8 * c)) & 255);
+                    ++c;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < M - 1; ++i)
+#pragma unroll
+                for (int j = 0; j < M - 1 - i; ++j) {
+                    const int32_t lo = min(f[j], f[j + 1]), hi = max(f[j], f[j + 1]);
+                    f[j] = lo;
+                    f[j + 1] = hi;
+                }
+            uint32_t loc = 0u - sbase;
+#pragma unroll
+            for (int a = 0; a < M; ++a) loc += (uint32_t)f[a] * bmul[a];
+            tile[(sl * TX + x) * P + y] = src[loc];
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            int sl, w;
+            if (tpow2) { sl = e >> (2 * ltx); w = e & (TX * TX - 1); }
+            else { sl = e / (TX * TX); w = e - sl * TX * TX; }
+            const int x = tpow2 ? (w & (TX - 1)) : w % TX, y = tpow2 ? (w >> ltx) : w / TX;
+            const int64_t sa = slab_addr[sl];
+            if (x >= xlim || y >= ylim || sa < 0) continue;
+            dense[base + sa + x + (int64_t)y * nas] = tile[(sl * TX + x) * P + y];
+        }
+    }
+}
+
+template <typename T>
+static int launch_unpack_tiled(const T* bcss, T* dense, int m, int64_t n, int b, int nbar, int64_t bm, int TX,
+                               int ntx, int slabs, int S, uint32_t ngrp, uint32_t total_units, size_t smem,
+                               cudaStream_t s)
+{
+    // 16-byte accesses for blocks without a repeated index: FP32, b, n and TX multiples
+    // of 4, both arrays 16-byte aligned
+    const int vec4 = (sizeof(T) == 4 && b % 4 == 0 && n % 4 == 0 && TX % 4 == 0 && ((uintptr_t)bcss & 15) == 0 &&
+                      ((uintptr_t)dense & 15) == 0) ? 1 : 0;
+    const int g = (int)(total_units < 152u * 8u ? total_units : 152u * 8u);
+    switch (m) {
+#define UT_CASE(MM)                                                                                             \
+    case MM:                                                                                                    \
+        bcss_unpack_tiled_kernel<T, MM><<<g, 256, smem, s>>>(bcss, dense, n, b, nbar, bm, TX, ntx, slabs, S,    \
+                                                             ngrp, total_units, vec4);                          \
+        break;
+        UT_CASE(2) UT_CASE(3) UT_CASE(4) UT_CASE(5) UT_CASE(6) UT_CASE(7) UT_CASE(8)
+#undef UT_CASE
+    default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
 int launch_bcss_pack(const void* dense, void* bcss, int m, int64_t n, int b, int dtype, cudaStream_t s)
 {
     int64_t nbar = (n + b - 1) / b;
@@ -183,6 +500,25 @@ int launch_bcss_pack(const void* dense, void* bcss, int m, int64_t n, int b, int
     // multiples of V and both arrays are 16-byte aligned (chunks are multiples of V)
     const int V = dtype == 0 ? 2 : 4;
     const int vec = (b % V == 0 && n % V == 0 && ((uintptr_t)dense & 15) == 0 && ((uintptr_t)bcss & 15) == 0) ? 1 : 0;
+    const size_t ctab_bytes = (size_t)m * nbar * sizeof(int64_t);
+    if (vec && m >= 1 && bm < ((int64_t)1 << 31) && ctab_bytes <= 32768) {
+        const int gg = (int)g;
+        const int nb = (int)nbar;
+        switch (m) {
+#define PK_CASE(MM)                                                                                                 \
+    case MM:                                                                                                        \
+        if (dtype == 0)                                                                                             \
+            bcss_pack_vec_kernel<double, MM><<<gg, threads, ctab_bytes, s>>>((const double*)dense, (double*)bcss, n, b, \
+                                                                          nb, nblocks, (uint32_t)bm);               \
+        else                                                                                                        \
+            bcss_pack_vec_kernel<float, MM><<<gg, threads, ctab_bytes, s>>>((const float*)dense, (float*)bcss, n, b, nb, \
+                                                                         nblocks, (uint32_t)bm);                    \
+        return (int)cudaGetLastError();
+            PK_CASE(1) PK_CASE(2) PK_CASE(3) PK_CASE(4) PK_CASE(5) PK_CASE(6) PK_CASE(7) PK_CASE(8)
+#undef PK_CASE
+        default: break;
+        }
+    }
     if (dtype == 0)
         bcss_pack_kernel<double><<<(int)g, threads, 0, s>>>((const double*)dense, (double*)bcss, m, n, b, nblocks, bm, vec);
     else
@@ -199,6 +535,37 @@ int launch_bcss_unpack(const void* bcss, void* dense, int m, int64_t n, int b, i
     const size_t tab_bytes = (size_t)m * (size_t)nbar * sizeof(int64_t);
     const int tab = tab_bytes <= 32768 ? 1 : 0;
     const size_t smem = tab ? tab_bytes : 0;
+    if (m >= 2 && b <= 256 && bm < ((int64_t)1 << 31)) {
+        // units: dense block x tile of TX x TX offsets (modes 0 and a*) x group of S slabs
+        // TX: b below 32, else the largest power of two <= 32 dividing b (no partial tiles)
+        int TX = b < 32 ? b : 32;
+        while (b >= 32 && b % TX != 0) TX >>= 1;
+        const int ntx = (b + TX - 1) / TX;
+        int64_t slabs = 1;
+        for (int a = 2; a < m; ++a) slabs *= b;
+        // groups of up to 8192 entries (several loads in flight per thread between
+        // barriers), tile <= 36 KB
+        const size_t esz = dtype == 0 ? sizeof(double) : sizeof(float);
+        int S = 8192 / (TX * TX);
+        const int s_bytes = (int)(36864 / ((size_t)TX * (TX + 1) * esz));
+        if (S > s_bytes) S = s_bytes;
+        if (S < 1) S = 1;
+        if ((int64_t)S > slabs) S = (int)slabs;
+        if (S > UT_MAX_SLABS) S = UT_MAX_SLABS;
+        const int64_t ngrp = (slabs + S - 1) / S;
+        int64_t nblk = 1;
+        for (int a = 0; a < m; ++a) nblk *= nbar;
+        const int64_t total_units = nblk * ntx * ntx * ngrp;
+        const size_t smem2 = (size_t)m * nbar * sizeof(int64_t) + (size_t)UT_MAX_SLABS * 16 +
+                             (size_t)S * TX * (TX + 1) * esz;
+        if (smem2 <= 48 * 1024 && total_units < ((int64_t)1 << 31)) {
+            if (dtype == 0)
+                return launch_unpack_tiled<double>((const double*)bcss, (double*)dense, m, n, b, (int)nbar, bm, TX,
+                                                   ntx, (int)slabs, S, (uint32_t)ngrp, (uint32_t)total_units, smem2, s);
+            return launch_unpack_tiled<float>((const float*)bcss, (float*)dense, m, n, b, (int)nbar, bm, TX, ntx,
+                                              (int)slabs, S, (uint32_t)ngrp, (uint32_t)total_units, smem2, s);
+        }
+    }
     int64_t g = (total + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
     if (dtype == 0)
@@ -497,20 +864,25 @@ __device__ __noinline__ void s32_issue_a_sym(S32Stage& S, const LevelInst& I, co
     for (int kk = I.Ktot; kk < Kc; ++kk) S.A[kk][threadIdx.x] = 0.f;
 }
 
-template <typename Desc>
+template <typename Desc, bool SYM>
 __device__ __forceinline__ void s32_issue(S32Stage& S, const Desc* insts, const LevelInst& inst0, const Tile& t,
                                           bool with_x)
 {
     const LevelInst& I = insts ? level_of(insts, t.inst) : inst0;
     const int Kc = (I.Ktot + 3) & ~3;
-    if (sym_tile(t.pad0)) {
-        switch (I.b) {
-        case 4: s32_issue_a_sym<4>(S, I, t, Kc); break;
-        case 8: s32_issue_a_sym<8>(S, I, t, Kc); break;
-        case 16: s32_issue_a_sym<16>(S, I, t, Kc); break;
-        default: s32_issue_a_sym<0>(S, I, t, Kc); break;
+    bool done = false;
+    if constexpr (SYM) {
+        if (sym_tile(t.pad0)) {
+            switch (I.b) {
+            case 4: s32_issue_a_sym<4>(S, I, t, Kc); break;
+            case 8: s32_issue_a_sym<8>(S, I, t, Kc); break;
+            case 16: s32_issue_a_sym<16>(S, I, t, Kc); break;
+            default: s32_issue_a_sym<0>(S, I, t, Kc); break;
+            }
+            done = true;
         }
-    } else switch (I.b) {
+    }
+    if (!done) switch (I.b) {
     case 4: s32_issue_a<4>(S, I, t, Kc); break;
     case 8: s32_issue_a<8>(S, I, t, Kc); break;
     case 16: s32_issue_a<16>(S, I, t, Kc); break;
@@ -777,7 +1149,7 @@ __device__ __noinline__ void s32_sym_row(S32Stage& S, const LevelInst& I, const 
 // A thread computes TR rows (t mod 128/TR, + 128/TR, ...) times NC/TR columns
 // (part t / (128/TR)), so every X value read from shared memory feeds TR
 // products; column pairs go through the two-lane FMA.
-template <int NC, int TR>
+template <int NC, int TR, bool SYM>
 __device__ __forceinline__ void s32_compute_store(S32Stage& S, const LevelInst& I, const Tile& t)
 {
     constexpr int TC = NC / TR, RSTEP = S32_ROWS / TR;
@@ -810,19 +1182,21 @@ __device__ __forceinline__ void s32_compute_store(S32Stage& S, const LevelInst& 
     const int b = I.b, bk = I.bpow[I.k];
     const int cfirst = t.col0 + part * TC;
     const int nvalid = t.ncols - part * TC;
-    if (sym_tile(t.pad0)) {
-        __syncthreads();   // every thread is done reading the operand stage
-#pragma unroll
-        for (int j = 0; j < TR; ++j)
-#pragma unroll
-            for (int e = 0; e < TC / 2; ++e) {
-                float lo, hi;
-                asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[j][e]));
-                S.A[part * TC + 2 * e][r0 + j * RSTEP] = lo;   // this thread's own cells
-                S.A[part * TC + 2 * e + 1][r0 + j * RSTEP] = hi;
-            }
-        s32_sym_store<TC, TR>(S, I, t, r0, part, cfirst, nvalid);
-        return;
+    if constexpr (SYM) {
+        if (sym_tile(t.pad0)) {
+            __syncthreads();   // every thread is done reading the operand stage
+    #pragma unroll
+            for (int j = 0; j < TR; ++j)
+    #pragma unroll
+                for (int e = 0; e < TC / 2; ++e) {
+                    float lo, hi;
+                    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[j][e]));
+                    S.A[part * TC + 2 * e][r0 + j * RSTEP] = lo;   // this thread's own cells
+                    S.A[part * TC + 2 * e + 1][r0 + j * RSTEP] = hi;
+                }
+            s32_sym_store<TC, TR>(S, I, t, r0, part, cfirst, nvalid);
+            return;
+        }
     }
     if (b >= 4 && (b & (b - 1)) == 0) {
         // b a power of two >= 4: a thread's columns start on a multiple of 4 and
@@ -881,19 +1255,21 @@ __device__ __forceinline__ void s32_compute_store(S32Stage& S, const LevelInst& 
 // columns in chunks of at most 16; the FP32 sum over each contraction block of
 // b indices is added to an FP64 sum (the cross-block accumulation of a C
 // block in FP64), and C gets the FP64 sum rounded once.
-template <int NC>
+template <int NC, bool SYM>
 __device__ __forceinline__ void s32_compute_store_r64(const S32Stage& S, const LevelInst& I, const Tile& t)
 {
     constexpr int CW = NC < 16 ? NC : 16;
     const int r = threadIdx.x;
-    const bool sym = sym_tile(t.pad0);
+    const bool sym = SYM && sym_tile(t.pad0);
     const int g = sym ? S.sym.g[r] : t.row0 + r;
     if (g < 0 || g >= I.rows_per_parent) return;
     const int Kc = (I.Ktot + 3) & ~3;
     const int b = I.b;
     const int pr = g / I.R, rr = g - pr * I.R;
     int32_t o[STTSM_MAX_M];
-    if (sym) s32_row_digits(I, rr, o);
+    if constexpr (SYM) {
+        if (sym) s32_row_digits(I, rr, o);
+    }
     float* row = (float*)I.out + ((int64_t)t.child_base * I.P_out + pr) * I.bm + __ldg(I.OFF + I.k * I.R + rr);
     const int64_t child_step = (int64_t)I.P_out * I.bm;
 #pragma unroll 1
@@ -932,9 +1308,11 @@ __device__ __forceinline__ void s32_compute_store_r64(const S32Stage& S, const L
         for (int e = 0; e < CW; ++e) {
             const int cc = t.col0 + c0 + e;
             if (c0 + e >= t.ncols) break;
-            if (sym) {
-                s32_sym_put(I, t, pr, __ldg(I.OFF + I.k * I.R + rr), o, S.sym.tie[r], cc, (float)dacc[e]);
-                continue;
+            if constexpr (SYM) {
+                if (sym) {
+                    s32_sym_put(I, t, pr, __ldg(I.OFF + I.k * I.R + rr), o, S.sym.tie[r], cc, (float)dacc[e]);
+                    continue;
+                }
             }
             const int jb = cc / b, c = cc - jb * b;
             row[(int64_t)jb * child_step + c] = (float)dacc[e];
@@ -942,7 +1320,9 @@ __device__ __forceinline__ void s32_compute_store_r64(const S32Stage& S, const L
     }
 }
 
-template <typename Desc>
+// SYM: the launch has tiles in the in-block-symmetry mode (sym.cuh); the other
+// instantiation carries none of that code and uses the stage without S32Sym.
+template <typename Desc, bool SYM>
 __global__ void __launch_bounds__(S32_ROWS, S32_CTAS_PER_SM)
 level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Tile* __restrict__ tiles, int ntiles,
                        int r64)
@@ -958,44 +1338,47 @@ level_small_f32_kernel(const Desc* __restrict__ insts, LevelInst inst0, const Ti
         const LevelInst& I = insts ? level_of(insts, t.inst) : inst0;
         const bool new_x = t.inst != x_inst || t.col0 != x_col0 || t.ncols != x_ncols;
         x_inst = t.inst; x_col0 = t.col0; x_ncols = t.ncols;
-        if (sym_tile(t.pad0)) {
-            if (!tab_ready) {
-                sym_tab_fill(S.sym.tab, threadIdx.x, blockDim.x);
-                __syncthreads();
-                tab_ready = true;
+        if constexpr (SYM) {
+            if (sym_tile(t.pad0)) {
+                if (!tab_ready) {
+                    sym_tab_fill(S.sym.tab, threadIdx.x, blockDim.x);
+                    __syncthreads();
+                    tab_ready = true;
+                }
+                s32_sym_row(S, I, t);   // read by the other threads after the barrier below
             }
-            s32_sym_row(S, I, t);   // read by the other threads after the barrier below
         }
-        s32_issue(S, insts, inst0, t, new_x);
+        s32_issue<Desc, SYM>(S, insts, inst0, t, new_x);
         s32_commit();
         s32_wait_all();
         __syncthreads();
         if (r64 && I.k == 0) {
             switch (s32_width_class(t.ncols)) {
-            case 0: s32_compute_store_r64<8>(S, I, t); break;
-            case 1: s32_compute_store_r64<16>(S, I, t); break;
-            case 2: s32_compute_store_r64<24>(S, I, t); break;
-            case 3: s32_compute_store_r64<32>(S, I, t); break;
-            case 4: s32_compute_store_r64<48>(S, I, t); break;
-            default: s32_compute_store_r64<64>(S, I, t); break;
+            case 0: s32_compute_store_r64<8, SYM>(S, I, t); break;
+            case 1: s32_compute_store_r64<16, SYM>(S, I, t); break;
+            case 2: s32_compute_store_r64<24, SYM>(S, I, t); break;
+            case 3: s32_compute_store_r64<32, SYM>(S, I, t); break;
+            case 4: s32_compute_store_r64<48, SYM>(S, I, t); break;
+            default: s32_compute_store_r64<64, SYM>(S, I, t); break;
             }
         } else switch (s32_width_class(t.ncols)) {
-        case 0: s32_compute_store<8, 1>(S, I, t); break;
-        case 1: s32_compute_store<16, 2>(S, I, t); break;
-        case 2: s32_compute_store<24, 2>(S, I, t); break;
-        case 3: s32_compute_store<32, 2>(S, I, t); break;
-        case 4: s32_compute_store<48, 4>(S, I, t); break;
-        default: s32_compute_store<64, 4>(S, I, t); break;
+        case 0: s32_compute_store<8, 1, SYM>(S, I, t); break;
+        case 1: s32_compute_store<16, 2, SYM>(S, I, t); break;
+        case 2: s32_compute_store<24, 2, SYM>(S, I, t); break;
+        case 3: s32_compute_store<32, 2, SYM>(S, I, t); break;
+        case 4: s32_compute_store<48, 4, SYM>(S, I, t); break;
+        default: s32_compute_store<64, 4, SYM>(S, I, t); break;
         }
         __syncthreads();
     }
 }
 
-template <typename Desc>
-static int launch_small_f32(const Desc* d_insts, const LevelInst& inst0, const Tile* d_tiles, int ntiles, int num_sms,
-                            cudaStream_t s, int r64)
+template <typename Desc, bool SYM>
+static int launch_small_f32_v(const Desc* d_insts, const LevelInst& inst0, const Tile* d_tiles, int ntiles,
+                              int num_sms, cudaStream_t s, int r64)
 {
-    if (ntiles <= 0) return 0;
+    // the stage without its S32Sym part unless the launch has symmetry-mode tiles
+    constexpr size_t smem = SYM ? S32_SMEM : offsetof(S32Stage, sym);
     static std::mutex mu;
     static bool attr_set[64] = {};
     int dev = 0;
@@ -1003,29 +1386,38 @@ static int launch_small_f32(const Desc* d_insts, const LevelInst& inst0, const T
     {
         std::lock_guard<std::mutex> lock(mu);
         if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-            const cudaError_t e = cudaFuncSetAttribute(level_small_f32_kernel<Desc>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S32_SMEM);
+            const cudaError_t e = cudaFuncSetAttribute(level_small_f32_kernel<Desc, SYM>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return (int)e;
             attr_set[dev] = true;
         }
     }
     const int grid = ntiles < num_sms * S32_CTAS_PER_SM ? ntiles : num_sms * S32_CTAS_PER_SM;
-    level_small_f32_kernel<Desc><<<grid, S32_ROWS, S32_SMEM, s>>>(d_insts, inst0, d_tiles, ntiles, r64);
+    level_small_f32_kernel<Desc, SYM><<<grid, S32_ROWS, smem, s>>>(d_insts, inst0, d_tiles, ntiles, r64);
     return (int)cudaGetLastError();
 }
 
-int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
-                           int num_sms, cudaStream_t s, int r64)
+template <typename Desc>
+static int launch_small_f32(const Desc* d_insts, const LevelInst& inst0, const Tile* d_tiles, int ntiles, int num_sms,
+                            cudaStream_t s, int r64, int sym)
 {
-    return launch_small_f32<LevelInst>(d_insts, inst0, d_tiles, ntiles, num_sms, s, r64);
+    if (ntiles <= 0) return 0;
+    return sym ? launch_small_f32_v<Desc, true>(d_insts, inst0, d_tiles, ntiles, num_sms, s, r64)
+               : launch_small_f32_v<Desc, false>(d_insts, inst0, d_tiles, ntiles, num_sms, s, r64);
+}
+
+int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
+                           int num_sms, cudaStream_t s, int r64, int sym)
+{
+    return launch_small_f32<LevelInst>(d_insts, inst0, d_tiles, ntiles, num_sms, s, r64, sym);
 }
 
 int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s,
-                              int r64)
+                              int r64, int sym)
 {
     LevelInst none;
     memset(&none, 0, sizeof(none));
-    return launch_small_f32<TcInst>(d_insts, none, d_tiles, ntiles, num_sms, s, r64);
+    return launch_small_f32<TcInst>(d_insts, none, d_tiles, ntiles, num_sms, s, r64, sym);
 }
 
 // ------------------------------------------------------------------ FP64 level kernel

@@ -45,13 +45,13 @@ int launch_level_tc_r64(int npiece, const TcInst& inst0, const TcInst* d_insts, 
 // FP32 CUDA-core kernel for short contractions (n̄ b <= 64): tiles of 128 rows
 // x <= 64 columns, X read from the instance's FP32 X (LevelInst::X).
 // r64: instances at their last level (k = 0) add the FP32 sums of their
-// contraction blocks in FP64 (the R64 precisions).  Tiles built by
-// build_level_tiles_sym (Tile::pad0 = SYM_TILE) compute canonical entries only
-// (in-block symmetry, sym.cuh); a launch may mix both kinds.
+// contraction blocks in FP64 (the R64 precisions).  sym: some tiles were built
+// by build_level_tiles_sym (Tile::pad0 = SYM_TILE: canonical entries only,
+// sym.cuh; a launch may mix both kinds); 0 runs the kernel without that code.
 int launch_level_small_f32(const LevelInst& inst0, const LevelInst* d_insts, const Tile* d_tiles, int ntiles,
-                           int num_sms, cudaStream_t s, int r64 = 0);
+                           int num_sms, cudaStream_t s, int r64 = 0, int sym = 0);
 int launch_level_small_f32_tc(const TcInst* d_insts, const Tile* d_tiles, int ntiles, int num_sms, cudaStream_t s,
-                              int r64 = 0);
+                              int r64 = 0, int sym = 0);
 
 // Levels m-2 and m-1 of short contractions fused (kernels_pair.cu): the
 // descriptor describes level m-2 with out = C; tiles from build_pair_tiles.

@@ -33,6 +33,7 @@
 #include <vector>
 #include "launch.h"
 #include "plan.h"
+#include "sym.cuh"
 #include "sttsm.h"
 
 using namespace sttsm;
@@ -401,12 +402,17 @@ int launch_step(sttsm_serve_s* H)
         const int n = (int)tiles[k].size();
         int lrc;
         int maxc = 0;
-        for (const Tile& t : tiles[k]) maxc = std::max(maxc, (int)t.ncols);
+        int symf = 0;
+        for (const Tile& t : tiles[k]) {
+            maxc = std::max(maxc, (int)t.ncols);
+            symf |= (t.pad0 & 3) == SYM_TILE ? 1 : 0;
+        }
         if (k == 0 && H->r64)
             lrc = launch_level_tc_r64(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, maxc, H->stream);
         else if (k == 0) lrc = launch_level_tc(H->np, dummy, (const TcInst*)(S.d + o_i[0]), dt, n, H->sms, H->status, H->stream);
         else if (k == 1 && (small_kernel_kind() == 0 || H->r64))
-            lrc = launch_level_small_f32_tc((const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->stream, H->r64 ? 1 : 0);
+            lrc = launch_level_small_f32_tc((const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->stream, H->r64 ? 1 : 0,
+                                            symf);
         else if (k == 1) lrc = launch_level_tc_small(H->np, dummy, (const TcInst*)(S.d + o_i[1]), dt, n, H->sms, H->status, H->stream);
         else if (k == 6) lrc = launch_level_pair_f32_tc((const TcInst*)(S.d + o_i[2]), dt, n, H->sms, H->stream);
         else {
