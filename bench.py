@@ -52,11 +52,13 @@ def parse_args():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16x6_r64", "bf16x3_r64"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
-    ap.add_argument("--workload", default="single", choices=["single", "m4", "abo", "batch", "serve", "symmetry"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "m4", "abo", "batch", "serve", "symmetry", "pack"],
                     help="single: m=3 n=p=768 instance (default); m4: m=4 n=128 p=64 compressing instance; "
                          "abo: all modes but one on the m=3 n=p=768 instance; batch: 4096 mixed instances; "
                          "serve: Poisson stream")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--pack-n", type=int, default=768, help="n of the m = 3 FP32 tensor of --workload pack")
     ap.add_argument("--ws-gb", type=float, default=48.0, help="batch workspace budget (GiB)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -186,21 +188,22 @@ def make_device_inputs(st, torch, b, dtype):
     return A
 
 
-def pack_bandwidth(st, torch, b, pk, pk_src, reps=5):
+def pack_bandwidth(st, torch, b, pk, pk_src, reps=5, n=None):
     """bcss_pack (dense -> BCSS) and bcss_unpack (BCSS -> dense) of the FP32
     workload tensor, CUDA events on the current stream, mean of reps launches
     after one untimed launch.  Algorithmic bytes: pack reads and writes each
     stored entry once (4 B each way); unpack writes each dense entry and reads
     its canonical stored entry (4 B each way)."""
     import synth
+    n = N if n is None else n
     stream = torch.cuda.current_stream()
-    dense = torch.empty(N ** M, dtype=torch.float32, device="cuda")
-    synth.dev_sym_uniform_dense(dense.data_ptr(), M, N, SEED_A, "f32", stream.cuda_stream)
-    A = torch.empty(st.bcss_num_elems(M, N, b), dtype=torch.float32, device="cuda")
+    dense = torch.empty(n ** M, dtype=torch.float32, device="cuda")
+    synth.dev_sym_uniform_dense(dense.data_ptr(), M, n, SEED_A, "f32", stream.cuda_stream)
+    A = torch.empty(st.bcss_num_elems(M, n, b), dtype=torch.float32, device="cuda")
     out = torch.empty_like(dense)
     res = {}
-    for name, fn, nbytes in (("pack", lambda: st.bcss_pack(dense, A, M, N, b), 8.0 * A.numel()),
-                             ("unpack", lambda: st.bcss_unpack(A, out, M, N, b), 8.0 * dense.numel())):
+    for name, fn, nbytes in (("pack", lambda: st.bcss_pack(dense, A, M, n, b), 8.0 * A.numel()),
+                             ("unpack", lambda: st.bcss_unpack(A, out, M, n, b), 8.0 * dense.numel())):
         fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1002,8 +1005,27 @@ def run_symmetry(args):
     return 0
 
 
+def run_pack(args):
+    """bcss_pack and bcss_unpack of the m = 3 FP32 symmetric tensor of dimension --pack-n
+    (block size --b, default 64): GB/s of algorithmic bytes and fraction of the measured
+    HBM copy peak, and the bit-exact round trip."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_7744_gb300 as st
+    pk, pk_src = peaks()
+    b = 64 if args.b == "auto" else int(args.b)
+    res = pack_bandwidth(st, torch, b, pk, pk_src, reps=5, n=args.pack_n)
+    print(json.dumps({"metric": "bcss pack / unpack GB/s", "unit": "GB/s", "higher_is_better": True,
+                      "config": {"workload": "pack_unpack", "m": M, "n": args.pack_n, "b": b, "dtype": "f32"},
+                      "results": res}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "pack":
+        return run_pack(args)
     if args.workload == "symmetry":
         return run_symmetry(args)
     if args.workload == "serve":
