@@ -415,6 +415,57 @@ bcss_unpack_tiled_kernel(const T* __restrict__ bcss, T* __restrict__ dense, int6
 #pragma unroll
         for (int a = 0; a < M; ++a) sbase += (uint32_t)sB[a] * (uint32_t)b * bmul[a];
         const int cnt = nslab * TX * TX;
+        if (vec4) {
+            // 4 consecutive entries along the read axis per iteration: one decode, four
+            // canonical-entry sorts and four independent loads
+            const int TX4 = TX >> 2;
+            const int cnt4 = nslab * TX * TX4;
+            const int lim_a = read_x ? xlim : ylim, lim_b = read_x ? ylim : xlim;   // limits along fa, fb
+            const int va = read_x ? 0 : as;   // the mode along which the 4 entries run
+            for (int e = threadIdx.x; e < cnt4; e += blockDim.x) {
+                const int sl = e / (TX * TX4), w = e - sl * TX * TX4;
+                const int fb = w / TX4, fa0 = (w - fb * TX4) * 4;
+                if (fa0 >= lim_a || fb >= lim_b || slab_addr[sl] < 0) continue;
+                const uint64_t offs = slab_off[sl];
+                int32_t f0[M];
+                int c = 0;
+#pragma unroll
+                for (int a = 0; a < M; ++a) {
+                    if (a == 0) {
+                        f0[a] = (int32_t)bx + (read_x ? fa0 : fb);
+                    } else if (a == as) {
+                        f0[a] = (int32_t)by + (read_x ? fb : fa0);
+                    } else {
+                        f0[a] = B[a] * b + (int)((offs >> (8 * c)) & 255);
+                        ++c;
+                    }
+                }
+                T v4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    int32_t f[M];
+#pragma unroll
+                    for (int a = 0; a < M; ++a) f[a] = f0[a] + (a == va ? u : 0);
+#pragma unroll
+                    for (int i = 0; i < M - 1; ++i)
+#pragma unroll
+                        for (int j = 0; j < M - 1 - i; ++j) {
+                            const int32_t lo = min(f[j], f[j + 1]), hi = max(f[j], f[j + 1]);
+                            f[j] = lo;
+                            f[j + 1] = hi;
+                        }
+                    uint32_t loc = 0u - sbase;
+#pragma unroll
+                    for (int a = 0; a < M; ++a) loc += (uint32_t)f[a] * bmul[a];
+                    v4[u] = src[loc];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int x = read_x ? fa0 + u : fb, y = read_x ? fb : fa0 + u;
+                    tile[(sl * TX + x) * P + y] = v4[u];
+                }
+            }
+        } else
 #pragma unroll 4
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
             int sl, w;
@@ -451,6 +502,20 @@ bcss_unpack_tiled_kernel(const T* __restrict__ bcss, T* __restrict__ dense, int6
             tile[(sl * TX + x) * P + y] = src[loc];
         }
         __syncthreads();
+        if (vec4) {
+            // the write side does not depend on the block: 4 consecutive x per store
+            const int TX4 = TX >> 2;
+            const int cnt4 = nslab * TX * TX4;
+            for (int e = threadIdx.x; e < cnt4; e += blockDim.x) {
+                const int sl = e / (TX * TX4), w = e - sl * TX * TX4;
+                const int y = w / TX4, x = (w - y * TX4) * 4;
+                const int64_t sa = slab_addr[sl];
+                if (x >= xlim || y >= ylim || sa < 0) continue;
+                const float* tp = (const float*)tile + (sl * TX + x) * P + y;
+                *(float4*)((float*)dense + base + sa + x + (int64_t)y * nas) = make_float4(tp[0], tp[P], tp[2 * P], tp[3 * P]);
+            }
+            continue;
+        }
 #pragma unroll 4
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
             int sl, w;
