@@ -605,6 +605,9 @@ int launch_bcss_unpack(const void* bcss, void* dense, int m, int64_t n, int b, i
         // TX: b below 32, else the largest power of two <= 32 dividing b (no partial tiles)
         int TX = b < 32 ? b : 32;
         while (b >= 32 && b % TX != 0) TX >>= 1;
+        // b between 32 and 64 that 32 does not divide (48, ...): one tile the block's width
+        // (rows of b, not 16, contiguous floats; 0.425 -> 0.49 of HBM at b = 48)
+        if (b > 32 && b < 64 && b % 32 != 0 && b % 4 == 0 && dtype == 1) TX = b;
         const int ntx = (b + TX - 1) / TX;
         int64_t slabs = 1;
         for (int a = 2; a < m; ++a) slabs *= b;
