@@ -76,7 +76,7 @@ def canonical_positions(m, n, b):
 
 @pytest.mark.parametrize("m,n,b", [(3, 96, 32), (3, 100, 32), (2, 64, 16), (2, 70, 32), (4, 24, 8), (4, 26, 8),
                                    (5, 16, 4), (3, 64, 64), (3, 48, 48), (3, 40, 12), (3, 36, 8), (3, 9, 4),
-                                   (6, 8, 4), (2, 300, 256)])
+                                   (6, 8, 4), (2, 300, 256), (3, 80, 40), (2, 120, 56), (3, 100, 48)])
 @pytest.mark.parametrize("dtname", ["f32", "f64"])
 def test_unpack_every_entry_is_its_canonical_entry(st, m, n, b, dtname):
     """bcss_unpack on stored blocks that are not symmetric inside (every stored entry
